@@ -1,0 +1,220 @@
+/*
+ * gnss.h -- C ABI of a B300 (sm_103a) GPS L1 C/A acquisition library.
+ *
+ * The library implements the acquisition channel of "Accelerating a
+ * Cloud-Based Software GNSS Receiver" (Karimi, Pamir, Afzal), Section 3,
+ * Fig. 2, as an FFT parallel code-phase search over a whole client
+ * recording: code NCO (Gold code + replica), carrier NCO and first mixing
+ * (wipe-off), FFT of the mixed signal and of the replica, frequency-domain
+ * second mixing, IFFT, |.|^2 summed non-coherently over blocks, and signal
+ * detection (peak against second peak).  The paper runs each ~1 ms FFT as a
+ * separate GPU call from many CPU threads (Section 5, Listing 3a); here a
+ * whole recording, all PRNs and all Doppler bins go to the device in one
+ * batched call (the batch mode of Listing 3b).
+ *
+ * Conventions shared by every entry point
+ *  - Status: every function returns a gnss_status; on failure
+ *    gnss_last_error() returns a message for the calling thread.  No C++
+ *    exception crosses this boundary.
+ *  - Ownership: the caller owns every buffer it passes.  Plans own their
+ *    device code tables; the library never hands out memory the caller must
+ *    free.  Scratch memory comes from a library-owned stream-ordered pool
+ *    (cudaMallocAsync) and is released in stream order.
+ *  - Streams: 'stream' is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Device-side work is enqueued on it; see each function
+ *    for when results are valid on the host.
+ *  - Devices: a plan belongs to the device that was current when it was
+ *    created; calls must be made with that device current.
+ *  - Recordings: complex baseband samples in one of two formats (below).
+ *    A device pointer to samples must be 16-byte aligned.
+ *  - Sample rate: fs is a multiple of 1000 Hz and N = fs / 1000 (the
+ *    samples of one 1 ms code period, the FFT size) is a power of two in
+ *    [256, 16384].
+ */
+#ifndef GNSS_H
+#define GNSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GNSS_API __attribute__((visibility("default")))
+#else
+#define GNSS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GNSS_OK = 0,
+  GNSS_EINVAL = 1,     /* bad argument, descriptor or length              */
+  GNSS_ENOMEM = 2,     /* host or device allocation failed                */
+  GNSS_ECUDA = 3,      /* a CUDA call failed (message in gnss_last_error) */
+  GNSS_EBUSY = 4,      /* over the server's memory budget / queue full    */
+  GNSS_EAGAIN = 5,     /* result not ready yet                            */
+  GNSS_ETIMEOUT = 6,   /* a bounded wait gave up                          */
+  GNSS_ECANCELLED = 7  /* request cancelled                               */
+} gnss_status;
+
+/* Recording formats.
+ * GNSS_FMT_I8_IQ:   int8 I, Q interleaved, 2 bytes per complex sample.
+ * GNSS_FMT_2BIT_IQ: 2-bit I/Q, two complex samples per byte,
+ *                   byte = I0 | Q0 << 2 | I1 << 4 | Q1 << 6, code c is the
+ *                   level 2c - 3 (-3, -1, +1, +3). */
+typedef enum { GNSS_FMT_I8_IQ = 0, GNSS_FMT_2BIT_IQ = 1 } gnss_format;
+
+/* Plan flags. */
+#define GNSS_HALF_BIT 0x1u     /* two non-coherent sets: even and odd blocks */
+#define GNSS_SECOND_WHOLE 0x2u /* second peak over the whole surface instead
+                                  of the peak's Doppler row (needs a surface) */
+
+/* Acquisition plan descriptor (Section 3, Fig. 2: sample rate and coherent
+ * length set the replica loop length fs * T; Doppler grid and PRN set define
+ * the search).
+ *  fs_hz        sample rate, multiple of 1000, fs/1000 a power of two 256..16384
+ *  coh_ms       coherent milliseconds per block T_coh >= 1 (folded before the FFT)
+ *  noncoh       blocks to sum non-coherently; 0 = every whole block recorded
+ *  dopp_min_hz, dopp_step_hz, n_dopp
+ *               Doppler bins f_d = dopp_min_hz + d * dopp_step_hz, d < n_dopp
+ *               (integer Hz; n_dopp >= 1, step >= 1 when n_dopp > 1)
+ *  prn_mask     bit p-1 set = search PRN p (1..32); at least one bit
+ *  threshold    detected = peak / second >= threshold (e.g. 2.0)
+ *  flags        GNSS_HALF_BIT | GNSS_SECOND_WHOLE
+ *  format       gnss_format of the recordings this plan will see */
+typedef struct {
+  uint32_t fs_hz;
+  uint32_t coh_ms;
+  uint32_t noncoh;
+  int32_t dopp_min_hz;
+  uint32_t dopp_step_hz;
+  uint32_t n_dopp;
+  uint64_t prn_mask;
+  float threshold;
+  uint32_t flags;
+  uint32_t format;
+  uint32_t reserved;
+} gnss_plan_desc;
+
+/* Detection record, one per searched PRN in ascending PRN order.
+ *  detected   peak / second >= threshold
+ *  set        non-coherent set the record comes from (0, or 1 = odd blocks
+ *             with GNSS_HALF_BIT; the set with the larger ratio, ties to 0)
+ *  dopp_bin   index d of the peak, dopp_hz its frequency
+ *  code_phase peak code phase in samples [0, N) (replica delay)
+ *  peak, second, ratio: surface values (sample units squared) and their ratio */
+typedef struct {
+  uint8_t prn;
+  uint8_t detected;
+  uint8_t set;
+  uint8_t reserved;
+  int32_t dopp_bin;
+  int32_t dopp_hz;
+  uint32_t code_phase;
+  float peak;
+  float second;
+  float ratio;
+} gnss_detection;
+
+/* Sizes a plan resolved from its descriptor. */
+typedef struct {
+  uint32_t N;          /* FFT size = fs / 1000                  */
+  uint32_t n_prn;      /* PRNs searched                         */
+  uint32_t n_dopp;     /* Doppler bins                          */
+  uint32_t n_sets;     /* 1, or 2 with GNSS_HALF_BIT            */
+  uint32_t excl;       /* second-peak exclusion half-width, ceil(N/1023) samples */
+  uint32_t block_len;  /* L = coh_ms * N samples per block      */
+} gnss_plan_info;
+
+typedef struct gnss_plan gnss_plan;
+
+/* Create a plan on the current device: validates the descriptor, generates
+ * the Gold codes of the searched PRNs on the device (G1 = 1 + x^3 + x^10,
+ * G2 = 1 + x^2 + x^3 + x^6 + x^8 + x^9 + x^10, both seeded all ones, two-tap
+ * G2 phase selector per PRN), samples each replica at fs
+ * (c_s[m] = c[floor(m * 1023 / N)]) and keeps its FFT resident (the code
+ * replica FFT of Fig. 2, computed once per plan instead of once per call).
+ * Synchronous.  On success *out owns device memory until gnss_plan_destroy.
+ * Errors: GNSS_EINVAL (descriptor), GNSS_ENOMEM, GNSS_ECUDA. */
+GNSS_API gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out);
+
+/* Release a plan (NULL is accepted).  The caller must make sure no work that
+ * uses the plan is still in flight. */
+GNSS_API gnss_status gnss_plan_destroy(gnss_plan* plan);
+
+/* Resolved sizes of a plan into *out (host). */
+GNSS_API gnss_status gnss_plan_get_info(const gnss_plan* plan, gnss_plan_info* out);
+
+/* Copy the plan's Gold codes to host memory: int8 [n_prn][1023] of +-1 chips
+ * (chip = 1 - 2 * bit), PRNs ascending.  cap = bytes available at out.
+ * Synchronous.  Errors: GNSS_EINVAL when cap < n_prn * 1023. */
+GNSS_API gnss_status gnss_plan_codes(const gnss_plan* plan, int8_t* out, size_t cap);
+
+/* Copy the plan's code spectra C_p[k] = FFT_N(c_s,p) (forward, unscaled) to
+ * device memory: float [n_prn][N][2] (re, im).  cap = bytes available.
+ * Enqueued on 'stream'. */
+GNSS_API gnss_status gnss_plan_code_spectra(const gnss_plan* plan, float* out_dev, size_t cap, void* stream);
+
+/* Bytes of the sample buffer that gnss_acquire reads for n_samples samples
+ * (only the B * L samples of whole blocks are read). */
+GNSS_API size_t gnss_recording_bytes(uint32_t format, size_t n_samples);
+
+/* Acquire every planned PRN over one recording (Section 3, Fig. 2, batched
+ * over the whole recording):
+ *   y_{f,b}[m] = sum_{i < T_coh} x[bL + iN + m] exp(-j 2 pi ((f (bL+iN+m)) mod fs) / fs)
+ *   R_{p,f,b}  = IFFT_N( FFT_N(y_{f,b}) * conj(C_p) ),   (inverse scaled 1/N)
+ *   S^{(s)}_{p,f}[tau] = sum over blocks b of set s of |R_{p,f,b}[tau]|^2,
+ * then per PRN the peak (largest cell, ties to the smallest Doppler-major
+ * index), the second peak (largest cell of the peak's Doppler row whose
+ * circular distance from the peak phase exceeds ceil(N/1023) samples) and
+ * their ratio.  B = floor(n_samples / L) blocks (capped by noncoh); trailing
+ * samples are ignored.
+ *  samples            recording in the plan's format; host memory, or device
+ *                     memory (16-byte aligned) when samples_on_device != 0
+ *  n_samples          complex samples in the recording (>= L)
+ *  out                host array of n_prn records (PRN ascending)
+ *  surface_dev        NULL, or device float [n_sets][n_prn][n_dopp][N] that
+ *                     receives the surfaces S
+ *  stream             work is enqueued on it; 'out' is valid once the stream
+ *                     has synchronised (a NULL stream is synchronised before
+ *                     the call returns)
+ * Errors: GNSS_EINVAL (n_samples < L, misaligned device pointer, NULL
+ * arguments), GNSS_ENOMEM, GNSS_ECUDA. */
+GNSS_API gnss_status gnss_acquire(gnss_plan* plan, const void* samples, size_t n_samples, int samples_on_device,
+                         gnss_detection* out, float* surface_dev, void* stream);
+
+/* Device-resident form of gnss_acquire: samples_dev and out_dev are device
+ * pointers; nothing is copied to or from the host and the call never
+ * synchronises.  Same arithmetic and errors. */
+GNSS_API gnss_status gnss_acquire_device(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                gnss_detection* out_dev, float* surface_dev, void* stream);
+
+/* Stage entry points (one launch each) for stage-level checks and for the
+ * one-stage-per-launch comparison.
+ * gnss_stage_wipe_fft: carrier wipe-off, coherent fold and forward FFT of
+ *   every (Doppler, block): spectra_dev = float [n_dopp][n_blocks][N][2],
+ *   Y_{f,b} = FFT_N(y_{f,b}).  n_blocks <= floor(n_samples / L).
+ * gnss_stage_correlate: conj-multiply with every code spectrum, IFFT, |.|^2
+ *   and the non-coherent sums over n_blocks blocks of spectra_dev; writes
+ *   surface_dev (may be NULL) and the per-PRN detections (device). */
+GNSS_API gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                uint32_t n_blocks, float* spectra_dev, void* stream);
+GNSS_API gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint32_t n_blocks,
+                                 float* surface_dev, gnss_detection* out_dev, void* stream);
+
+/* FP32 FMA throughput probe (a measurement aid with no counterpart in the
+ * paper; it states the ALU roof the acquisition kernels are held against):
+ * 'iters' rounds of 128 dependent-chain FMAs per thread, 4 CTAs of 512
+ * threads per SM.  Writes TFLOP/s (2 flops per FMA) and the kernel time in
+ * ms (ms may be NULL).  Synchronous. */
+GNSS_API gnss_status gnss_probe_ffma(int iters, double* tflops, double* ms, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+GNSS_API const char* gnss_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GNSS_H */

@@ -1,0 +1,223 @@
+"""Python binding of the B300 GPS L1 C/A acquisition library (libgnss.so).
+
+Argument marshalling only: every step of the acquisition runs in the CUDA
+kernels behind the C ABI declared in include/gnss.h.  Device buffers are
+torch CUDA tensors (their data_ptr() is passed through); host buffers are
+numpy arrays.  There is no CPU fallback: importing this package fails
+loudly when the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgnss.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, EAGAIN, ETIMEOUT, ECANCELLED = range(8)
+STATUS_NAMES = ["GNSS_OK", "GNSS_EINVAL", "GNSS_ENOMEM", "GNSS_ECUDA", "GNSS_EBUSY", "GNSS_EAGAIN",
+                "GNSS_ETIMEOUT", "GNSS_ECANCELLED"]
+FMT_I8_IQ = 0
+FMT_2BIT_IQ = 1
+HALF_BIT = 0x1
+SECOND_WHOLE = 0x2
+
+
+class PlanDesc(C.Structure):
+    _fields_ = [("fs_hz", C.c_uint32), ("coh_ms", C.c_uint32), ("noncoh", C.c_uint32),
+                ("dopp_min_hz", C.c_int32), ("dopp_step_hz", C.c_uint32), ("n_dopp", C.c_uint32),
+                ("prn_mask", C.c_uint64), ("threshold", C.c_float), ("flags", C.c_uint32),
+                ("format", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("N", C.c_uint32), ("n_prn", C.c_uint32), ("n_dopp", C.c_uint32), ("n_sets", C.c_uint32),
+                ("excl", C.c_uint32), ("block_len", C.c_uint32)]
+
+
+DETECTION_DTYPE = np.dtype([("prn", "u1"), ("detected", "u1"), ("set", "u1"), ("reserved", "u1"),
+                            ("dopp_bin", "<i4"), ("dopp_hz", "<i4"), ("code_phase", "<u4"),
+                            ("peak", "<f4"), ("second", "<f4"), ("ratio", "<f4")])
+assert DETECTION_DTYPE.itemsize == 28
+
+_P = C.c_void_p
+_st = C.c_int
+_SIGS = {
+    "gnss_plan_create": ([C.POINTER(PlanDesc), C.POINTER(_P)], _st),
+    "gnss_plan_destroy": ([_P], _st),
+    "gnss_plan_get_info": ([_P, C.POINTER(PlanInfo)], _st),
+    "gnss_plan_codes": ([_P, _P, C.c_size_t], _st),
+    "gnss_plan_code_spectra": ([_P, _P, C.c_size_t, _P], _st),
+    "gnss_recording_bytes": ([C.c_uint32, C.c_size_t], C.c_size_t),
+    "gnss_acquire": ([_P, _P, C.c_size_t, C.c_int, _P, _P, _P], _st),
+    "gnss_acquire_device": ([_P, _P, C.c_size_t, _P, _P, _P], _st),
+    "gnss_stage_wipe_fft": ([_P, _P, C.c_size_t, C.c_uint32, _P, _P], _st),
+    "gnss_stage_correlate": ([_P, _P, C.c_uint32, _P, _P, _P], _st),
+    "gnss_probe_ffma": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], _st),
+    "gnss_last_error": ([], C.c_char_p),
+}
+_lib = None
+
+
+def load():
+    """Load libgnss.so (once).  Raises ImportError when it has not been built:
+    there is no CPU fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libgnss.so is not built: run `python -m paper_1309_0052_b300.build` "
+                              "(or __graft_entry__.build()) first; there is no CPU fallback")
+        handle = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = handle
+    return _lib
+
+
+def __getattr__(name):
+    if name == "lib":
+        return load()
+    raise AttributeError(name)
+
+
+class GnssError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = load().gnss_last_error().decode(errors="replace")
+        super().__init__("%s failed: %s: %s" % (where, STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+
+
+def check(status: int, where: str) -> None:
+    if status != OK:
+        raise GnssError(status, where)
+
+
+def _ptr(obj) -> int | None:
+    """Address of a torch tensor (device or host), numpy array or bytes; None for None."""
+    if obj is None:
+        return None
+    if hasattr(obj, "data_ptr"):
+        return obj.data_ptr()
+    if isinstance(obj, np.ndarray):
+        return obj.ctypes.data
+    raise TypeError("expected a torch tensor or a numpy array")
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def recording_bytes(fmt: int, n_samples: int) -> int:
+    return load().gnss_recording_bytes(fmt, n_samples)
+
+
+def prn_mask(prns) -> int:
+    m = 0
+    for p in prns:
+        m |= 1 << (int(p) - 1)
+    return m
+
+
+class Plan:
+    """An acquisition plan (gnss_plan_create): Gold codes and code spectra of
+    the searched PRNs resident on the current device."""
+
+    def __init__(self, fs_hz: int, coh_ms: int, dopp_min_hz: int, dopp_step_hz: int, n_dopp: int,
+                 prns=range(1, 33), noncoh: int = 0, threshold: float = 2.0, half_bit: bool = False,
+                 second_whole: bool = False, fmt: int = FMT_2BIT_IQ):
+        self.desc = PlanDesc(fs_hz=fs_hz, coh_ms=coh_ms, noncoh=noncoh, dopp_min_hz=dopp_min_hz,
+                             dopp_step_hz=dopp_step_hz, n_dopp=n_dopp, prn_mask=prn_mask(prns),
+                             threshold=threshold,
+                             flags=(HALF_BIT if half_bit else 0) | (SECOND_WHOLE if second_whole else 0),
+                             format=fmt)
+        h = _P()
+        check(load().gnss_plan_create(C.byref(self.desc), C.byref(h)), "gnss_plan_create")
+        self._h = h
+        info = PlanInfo()
+        check(load().gnss_plan_get_info(h, C.byref(info)), "gnss_plan_get_info")
+        self.N, self.n_prn, self.n_dopp, self.n_sets = info.N, info.n_prn, info.n_dopp, info.n_sets
+        self.excl, self.block_len = info.excl, info.block_len
+        self.fmt = fmt
+
+    @classmethod
+    def for_recording(cls, rec, prns=range(1, 33), **kw):
+        """Plan matching a siggen.Recording's workload parameters."""
+        return cls(rec.fs, rec.coh_ms, rec.dopp_min_hz, rec.dopp_step_hz, rec.n_dopp, prns=prns,
+                   noncoh=rec.noncoh, half_bit=rec.half_bit, fmt=rec.fmt, **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gnss_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def n_blocks(self, n_samples: int) -> int:
+        B = n_samples // self.block_len
+        return min(B, self.desc.noncoh) if self.desc.noncoh else B
+
+    def codes(self) -> np.ndarray:
+        out = np.zeros((self.n_prn, 1023), np.int8)
+        check(load().gnss_plan_codes(self._h, out.ctypes.data, out.nbytes), "gnss_plan_codes")
+        return out
+
+    def code_spectra(self, out, stream=None):
+        """Copy C_p into a float32 CUDA tensor [n_prn, N, 2]."""
+        check(load().gnss_plan_code_spectra(self._h, _ptr(out), out.numel() * 4, _stream_ptr(stream)),
+              "gnss_plan_code_spectra")
+        return out
+
+    def surface_shape(self):
+        return (self.n_sets, self.n_prn, self.n_dopp, self.N)
+
+    def acquire(self, samples, n_samples: int, surface=None, stream=None) -> np.ndarray:
+        """gnss_acquire.  samples: numpy (host) or CUDA tensor (device).
+        Returns the detection records; synchronises the stream."""
+        out = np.zeros(self.n_prn, DETECTION_DTYPE)
+        on_dev = int(hasattr(samples, "is_cuda") and samples.is_cuda)
+        if not on_dev:
+            samples = np.ascontiguousarray(samples)
+        check(load().gnss_acquire(self._h, _ptr(samples), n_samples, on_dev, out.ctypes.data, _ptr(surface),
+                               _stream_ptr(stream)), "gnss_acquire")
+        if stream is not None:
+            stream.synchronize()
+        return out
+
+    def acquire_device(self, samples_dev, n_samples: int, out_dev, surface=None, stream=None) -> None:
+        """gnss_acquire_device: out_dev is a CUDA uint8 tensor of n_prn * 28 bytes."""
+        check(load().gnss_acquire_device(self._h, _ptr(samples_dev), n_samples, _ptr(out_dev), _ptr(surface),
+                                      _stream_ptr(stream)), "gnss_acquire_device")
+
+    def stage_wipe_fft(self, samples_dev, n_samples: int, n_blocks: int, spectra_dev, stream=None) -> None:
+        check(load().gnss_stage_wipe_fft(self._h, _ptr(samples_dev), n_samples, n_blocks, _ptr(spectra_dev),
+                                      _stream_ptr(stream)), "gnss_stage_wipe_fft")
+
+    def stage_correlate(self, spectra_dev, n_blocks: int, out_dev, surface=None, stream=None) -> None:
+        check(load().gnss_stage_correlate(self._h, _ptr(spectra_dev), n_blocks, _ptr(surface), _ptr(out_dev),
+                                       _stream_ptr(stream)), "gnss_stage_correlate")
+
+
+def probe_ffma(iters: int = 4096, stream=None):
+    """Measured FP32 FMA throughput (TFLOP/s) and kernel time (ms)."""
+    tf, ms = C.c_double(), C.c_double()
+    check(load().gnss_probe_ffma(iters, C.byref(tf), C.byref(ms), _stream_ptr(stream)), "gnss_probe_ffma")
+    return tf.value, ms.value
+
+
+def detections_from_bytes(buf) -> np.ndarray:
+    """View a device-side detection buffer copied to host (uint8) as records."""
+    return np.frombuffer(np.asarray(buf, np.uint8).tobytes(), DETECTION_DTYPE)

@@ -1,0 +1,298 @@
+// capi.cu -- C ABI of the acquisition library (include/gnss.h): plans,
+// acquisition entry points, stage entry points, errors and scratch memory.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace gnss {
+
+static thread_local std::string t_error;
+
+void set_error(const std::string& msg) { t_error = msg; }
+
+static gnss_status fail(gnss_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+static gnss_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(GNSS_ECUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+// Library-owned stream-ordered pool per device, keeping freed blocks cached
+// so that repeated acquisitions do not return memory to the driver.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[128];
+static bool g_pool_ok[128];
+
+static cudaError_t device_pool(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool_ok[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaError_t e = cudaMemPoolCreate(&g_pool[dev], &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) return e;
+    g_pool_ok[dev] = true;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+static gnss_status scratch_alloc(int dev, size_t bytes, cudaStream_t stream, void** out) {
+  cudaMemPool_t pool;
+  cudaError_t e = device_pool(dev, &pool);
+  if (e != cudaSuccess) return cuda_fail(e, "memory pool");
+  e = cudaMallocFromPoolAsync(out, bytes, pool, stream);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(GNSS_ENOMEM, "device scratch allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync");
+  return GNSS_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static gnss_status check_device(const gnss_plan* plan) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != plan->device) return fail(GNSS_EINVAL, "plan belongs to another device than the current one");
+  return GNSS_OK;
+}
+
+static AcqShape shape_of(const gnss_plan* plan, int B) {
+  AcqShape s;
+  s.fs = (int)plan->desc.fs_hz;
+  s.N = plan->N;
+  s.coh = (int)plan->desc.coh_ms;
+  s.B = B;
+  s.D = plan->D;
+  s.P = plan->P;
+  s.sets = plan->sets;
+  s.excl = plan->excl;
+  s.dopp_min = plan->desc.dopp_min_hz;
+  s.dopp_step = (int)plan->desc.dopp_step_hz;
+  s.format = (int)plan->desc.format;
+  s.second_whole = (plan->desc.flags & GNSS_SECOND_WHOLE) ? 1 : 0;
+  s.threshold = plan->desc.threshold;
+  return s;
+}
+
+static int blocks_of(const gnss_plan* plan, size_t n_samples) {
+  const size_t L = (size_t)plan->desc.coh_ms * plan->N;
+  size_t B = n_samples / L;
+  if (plan->desc.noncoh && B > plan->desc.noncoh) B = plan->desc.noncoh;
+  if (B > (size_t)INT32_MAX) B = INT32_MAX;
+  return (int)B;
+}
+
+static size_t rec_bytes(uint32_t format, size_t n) {
+  return format == GNSS_FMT_I8_IQ ? 2 * n : (n + 1) / 2;
+}
+
+// Shared body of gnss_acquire / gnss_acquire_device.
+static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_samples, int samples_on_device,
+                                gnss_detection* out_host, gnss_detection* out_dev, float* surface_dev,
+                                cudaStream_t stream) {
+  if (!plan || !samples || (!out_host && !out_dev)) return fail(GNSS_EINVAL, "NULL argument");
+  gnss_status st = check_device(plan);
+  if (st != GNSS_OK) return st;
+  const int B = blocks_of(plan, n_samples);
+  if (B < 1) return fail(GNSS_EINVAL, "n_samples is shorter than one coherent block");
+  if (samples_on_device && ((uintptr_t)samples & 15u)) return fail(GNSS_EINVAL, "device samples must be 16-byte aligned");
+  if ((plan->desc.flags & GNSS_SECOND_WHOLE) && !surface_dev)
+    return fail(GNSS_EINVAL, "GNSS_SECOND_WHOLE needs a surface buffer");
+  const AcqShape s = shape_of(plan, B);
+  const size_t y_bytes = align256((size_t)s.D * s.B * s.N * sizeof(float2));
+  const size_t row_bytes = align256((size_t)s.sets * s.P * s.D * sizeof(RowStat));
+  const size_t det_bytes = align256((size_t)s.P * sizeof(gnss_detection));
+  const size_t smp_bytes = samples_on_device ? 0 : align256(rec_bytes(plan->desc.format, (size_t)B * s.coh * s.N));
+  char* ws = nullptr;
+  st = scratch_alloc(plan->device, y_bytes + row_bytes + det_bytes + smp_bytes, stream, (void**)&ws);
+  if (st != GNSS_OK) return st;
+  float2* d_Y = reinterpret_cast<float2*>(ws);
+  RowStat* d_rows = reinterpret_cast<RowStat*>(ws + y_bytes);
+  gnss_detection* d_det = out_dev ? out_dev : reinterpret_cast<gnss_detection*>(ws + y_bytes + row_bytes);
+  const uint8_t* d_smp = reinterpret_cast<const uint8_t*>(samples);
+  cudaError_t e = cudaSuccess;
+  if (!samples_on_device) {
+    uint8_t* dst = reinterpret_cast<uint8_t*>(ws + y_bytes + row_bytes + det_bytes);
+    e = cudaMemcpyAsync(dst, samples, rec_bytes(plan->desc.format, (size_t)B * s.coh * s.N),
+                        cudaMemcpyHostToDevice, stream);
+    d_smp = dst;
+  }
+  if (e == cudaSuccess) e = launch_wipe_fft(s, d_smp, d_Y, stream);
+  if (e == cudaSuccess) e = launch_xcorr(s, d_Y, plan->d_cspec, surface_dev, d_rows, stream);
+  if (e == cudaSuccess) e = launch_peak(s, d_rows, plan->d_prns, surface_dev, d_det, stream);
+  if (e == cudaSuccess && out_host)
+    e = cudaMemcpyAsync(out_host, d_det, (size_t)s.P * sizeof(gnss_detection), cudaMemcpyDeviceToHost, stream);
+  cudaError_t ef = cudaFreeAsync(ws, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "acquire");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  if (stream == nullptr && out_host) {
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  }
+  return GNSS_OK;
+}
+
+}  // namespace gnss
+
+using namespace gnss;
+
+extern "C" {
+
+const char* gnss_last_error(void) { return t_error.c_str(); }
+
+size_t gnss_recording_bytes(uint32_t format, size_t n_samples) { return rec_bytes(format, n_samples); }
+
+gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
+  if (!desc || !out) return fail(GNSS_EINVAL, "NULL argument");
+  *out = nullptr;
+  const gnss_plan_desc& d = *desc;
+  if (d.fs_hz == 0 || d.fs_hz % 1000) return fail(GNSS_EINVAL, "fs_hz must be a positive multiple of 1000");
+  const int N = (int)(d.fs_hz / 1000);
+  if (!supported_fft_size(N)) return fail(GNSS_EINVAL, "fs_hz / 1000 must be a power of two in [256, 16384]");
+  if (d.coh_ms < 1 || d.coh_ms > 100000) return fail(GNSS_EINVAL, "coh_ms must be in [1, 100000]");
+  if (d.n_dopp < 1 || d.n_dopp > 100000) return fail(GNSS_EINVAL, "n_dopp must be in [1, 100000]");
+  if (d.n_dopp > 1 && d.dopp_step_hz < 1) return fail(GNSS_EINVAL, "dopp_step_hz must be >= 1");
+  const int64_t fmax = (int64_t)d.dopp_min_hz + (int64_t)(d.n_dopp - 1) * d.dopp_step_hz;
+  if (fmax > INT32_MAX / 2 || (int64_t)d.dopp_min_hz < INT32_MIN / 2) return fail(GNSS_EINVAL, "Doppler grid out of range");
+  if ((d.prn_mask & 0xFFFFFFFFull) == 0 || (d.prn_mask >> 32)) return fail(GNSS_EINVAL, "prn_mask must select PRNs within 1..32");
+  if (d.format != GNSS_FMT_I8_IQ && d.format != GNSS_FMT_2BIT_IQ) return fail(GNSS_EINVAL, "unknown format");
+  if (d.flags & ~(GNSS_HALF_BIT | GNSS_SECOND_WHOLE)) return fail(GNSS_EINVAL, "unknown flags");
+  if (!(d.threshold >= 0.f) || isinf(d.threshold)) return fail(GNSS_EINVAL, "threshold must be finite and >= 0");
+
+  gnss_plan* p = new (std::nothrow) gnss_plan;
+  if (!p) return fail(GNSS_ENOMEM, "host allocation failed");
+  memset(p, 0, sizeof(*p));
+  p->desc = d;
+  p->N = N;
+  p->D = (int)d.n_dopp;
+  p->sets = (d.flags & GNSS_HALF_BIT) ? 2 : 1;
+  p->excl = (N + 1022) / 1023;
+  for (int prn = 1; prn <= 32; ++prn)
+    if (d.prn_mask >> (prn - 1) & 1ull) p->prns[p->P++] = prn;
+  cudaError_t e = cudaGetDevice(&p->device);
+  cudaStream_t st = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_prns, sizeof(int) * p->P);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_codes, (size_t)p->P * 1023);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_cspec, (size_t)p->P * N * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_prns, p->prns, sizeof(int) * p->P, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_gold(p->d_prns, p->P, p->d_codes, st);
+  if (e == cudaSuccess) e = launch_code_spectra(p->d_codes, p->P, N, p->d_cspec, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (st) cudaStreamDestroy(st);
+  if (e != cudaSuccess) {
+    gnss_status r = (e == cudaErrorMemoryAllocation) ? fail(GNSS_ENOMEM, "device allocation failed")
+                                                      : cuda_fail(e, "gnss_plan_create");
+    cudaFree(p->d_prns);
+    cudaFree(p->d_codes);
+    cudaFree(p->d_cspec);
+    delete p;
+    return r;
+  }
+  *out = p;
+  return GNSS_OK;
+}
+
+gnss_status gnss_plan_destroy(gnss_plan* plan) {
+  if (!plan) return GNSS_OK;
+  cudaFree(plan->d_prns);
+  cudaFree(plan->d_codes);
+  cudaFree(plan->d_cspec);
+  delete plan;
+  return GNSS_OK;
+}
+
+gnss_status gnss_plan_get_info(const gnss_plan* plan, gnss_plan_info* out) {
+  if (!plan || !out) return fail(GNSS_EINVAL, "NULL argument");
+  out->N = (uint32_t)plan->N;
+  out->n_prn = (uint32_t)plan->P;
+  out->n_dopp = (uint32_t)plan->D;
+  out->n_sets = (uint32_t)plan->sets;
+  out->excl = (uint32_t)plan->excl;
+  out->block_len = plan->desc.coh_ms * (uint32_t)plan->N;
+  return GNSS_OK;
+}
+
+gnss_status gnss_plan_codes(const gnss_plan* plan, int8_t* out, size_t cap) {
+  if (!plan || !out) return fail(GNSS_EINVAL, "NULL argument");
+  if (cap < (size_t)plan->P * 1023) return fail(GNSS_EINVAL, "output too small");
+  cudaError_t e = cudaMemcpy(out, plan->d_codes, (size_t)plan->P * 1023, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "gnss_plan_codes");
+  return GNSS_OK;
+}
+
+gnss_status gnss_plan_code_spectra(const gnss_plan* plan, float* out_dev, size_t cap, void* stream) {
+  if (!plan || !out_dev) return fail(GNSS_EINVAL, "NULL argument");
+  const size_t bytes = (size_t)plan->P * plan->N * sizeof(float2);
+  if (cap < bytes) return fail(GNSS_EINVAL, "output too small");
+  cudaError_t e = cudaMemcpyAsync(out_dev, plan->d_cspec, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gnss_plan_code_spectra");
+  return GNSS_OK;
+}
+
+gnss_status gnss_acquire(gnss_plan* plan, const void* samples, size_t n_samples, int samples_on_device,
+                         gnss_detection* out, float* surface_dev, void* stream) {
+  return acquire_impl(plan, samples, n_samples, samples_on_device, out, nullptr, surface_dev, (cudaStream_t)stream);
+}
+
+gnss_status gnss_acquire_device(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                gnss_detection* out_dev, float* surface_dev, void* stream) {
+  if (!out_dev) return fail(GNSS_EINVAL, "NULL argument");
+  return acquire_impl(plan, samples_dev, n_samples, 1, nullptr, out_dev, surface_dev, (cudaStream_t)stream);
+}
+
+gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_dev, size_t n_samples, uint32_t n_blocks,
+                                float* spectra_dev, void* stream) {
+  if (!plan || !samples_dev || !spectra_dev) return fail(GNSS_EINVAL, "NULL argument");
+  gnss_status st = check_device(plan);
+  if (st != GNSS_OK) return st;
+  if ((uintptr_t)samples_dev & 15u) return fail(GNSS_EINVAL, "device samples must be 16-byte aligned");
+  const size_t L = (size_t)plan->desc.coh_ms * plan->N;
+  if (n_blocks < 1 || (size_t)n_blocks > n_samples / L) return fail(GNSS_EINVAL, "n_blocks out of range");
+  const AcqShape s = shape_of(plan, (int)n_blocks);
+  cudaError_t e = launch_wipe_fft(s, (const uint8_t*)samples_dev, (float2*)spectra_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gnss_stage_wipe_fft");
+  return GNSS_OK;
+}
+
+gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint32_t n_blocks, float* surface_dev,
+                                 gnss_detection* out_dev, void* stream) {
+  if (!plan || !spectra_dev || !out_dev || n_blocks < 1) return fail(GNSS_EINVAL, "bad argument");
+  gnss_status st = check_device(plan);
+  if (st != GNSS_OK) return st;
+  if ((plan->desc.flags & GNSS_SECOND_WHOLE) && !surface_dev)
+    return fail(GNSS_EINVAL, "GNSS_SECOND_WHOLE needs a surface buffer");
+  const AcqShape s = shape_of(plan, (int)n_blocks);
+  cudaStream_t cs = (cudaStream_t)stream;
+  RowStat* rows = nullptr;
+  st = scratch_alloc(plan->device, (size_t)s.sets * s.P * s.D * sizeof(RowStat), cs, (void**)&rows);
+  if (st != GNSS_OK) return st;
+  cudaError_t e = launch_xcorr(s, (const float2*)spectra_dev, plan->d_cspec, surface_dev, rows, cs);
+  if (e == cudaSuccess) e = launch_peak(s, rows, plan->d_prns, surface_dev, out_dev, cs);
+  cudaError_t ef = cudaFreeAsync(rows, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "gnss_stage_correlate");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return GNSS_OK;
+}
+
+}  // extern "C"

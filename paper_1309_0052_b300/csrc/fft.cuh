@@ -1,0 +1,236 @@
+// fft.cuh -- register-resident mixed-radix Stockham FFT for one CTA (sm_103a).
+//
+// The FFT / IFFT blocks of the acquisition channel (Section 3, Fig. 2).
+// One CTA of T = N / E threads transforms one N-point complex vector.  Thread
+// j always holds the E elements x[j + T r], r < E, in registers:
+//   - every Stockham pass reads its butterfly inputs J + s N / R, which for
+//     J = j + T q are exactly x[j + T (q + (E/R) s)], so the first pass of a
+//     transform starts from registers without any shared-memory traffic;
+//   - the last pass writes its outputs J + t N / R = j + T (q + (E/R) t),
+//     again the thread's own registers, in natural order;
+//   - the P - 1 passes in between exchange through shared memory (padded
+//     index i + i/16, so the stride-16 writes of the first pass and the
+//     unit-stride reads are free of bank conflicts).
+// Radix-16 passes come first, then one radix-2/4/8 pass for the rest of N.
+//
+// Pass with sub-transform size NS and radix R (Stockham autosort): for
+// butterfly J < N/R, k = J mod NS,
+//   u[s] = x[J + s N/R] * W_{NS R}^{s k},   u <- DFT_R(u),
+//   y[(J / NS) NS R + k + t NS] = u[t].
+// Forward W = exp(-2 pi i / M) unscaled; inverse W = exp(+2 pi i / M), the
+// caller applies 1/N.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gnss {
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 c_mulconj(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// multiply by the quarter-turn of the transform direction: -i (forward), +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 c_quarter(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos / sin of k pi / 8 (mathematical constants of the 16-point transform)
+#define GNSS_C1 0.92387953251128675613f  // cos(pi/8)
+#define GNSS_S1 0.38268343236508977173f  // sin(pi/8)
+#define GNSS_R2 0.70710678118654752440f  // sqrt(2)/2
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = c_add(t, b);
+  b = c_sub(t, b);
+}
+
+// 4-point DFT in place, natural order.
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 s0 = c_add(x0, x2), d0 = c_sub(x0, x2);
+  float2 s1 = c_add(x1, x3), d1 = c_quarter<INV>(c_sub(x1, x3));
+  x0 = c_add(s0, s1);
+  x2 = c_sub(s0, s1);
+  x1 = c_add(d0, d1);
+  x3 = c_sub(d0, d1);
+}
+
+// multiply by W_M^m with W_M = exp(-+2 pi i / M) for the constant angles of
+// the 8- and 16-point transforms (m * 16 / M in 0..9 sixteenths of a turn).
+template <bool INV, int SIXTEENTHS>
+__device__ __forceinline__ float2 twiddle16(float2 a) {
+  constexpr float sg = INV ? 1.f : -1.f;
+  if constexpr (SIXTEENTHS == 0) return a;
+  else if constexpr (SIXTEENTHS == 4) return c_quarter<INV>(a);
+  else if constexpr (SIXTEENTHS == 2) {  // (1 + sg i) / sqrt 2
+    return make_float2(GNSS_R2 * (a.x - sg * a.y), GNSS_R2 * (a.y + sg * a.x));
+  } else if constexpr (SIXTEENTHS == 6) {  // (-1 + sg i) / sqrt 2
+    return make_float2(GNSS_R2 * (-a.x - sg * a.y), GNSS_R2 * (-a.y + sg * a.x));
+  } else {
+    constexpr float c = SIXTEENTHS == 1 ? GNSS_C1 : SIXTEENTHS == 3 ? GNSS_S1 : -GNSS_C1;
+    constexpr float s = SIXTEENTHS == 1 ? GNSS_S1 : SIXTEENTHS == 3 ? GNSS_C1 : -GNSS_S1;
+    return c_mul(a, make_float2(c, sg * s));
+  }
+}
+
+// 8-point DFT: n = n2 + 4 n1, k = k1 + 2 k2.  Radix-2 over n1, twiddle
+// W8^(n2 k1), radix-4 over n2.  Output X[k1 + 2 k2] lands in v[4 k1 + k2];
+// the caller-visible order is restored by the final register permutation.
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft2<INV>(v[n2], v[n2 + 4]);  // v[n2 + 4 k1]
+  v[5] = twiddle16<INV, 2>(v[5]);
+  v[6] = twiddle16<INV, 4>(v[6]);
+  v[7] = twiddle16<INV, 6>(v[7]);
+  dft4<INV>(v[0], v[1], v[2], v[3]);  // k1 = 0 -> X[2 k2]
+  dft4<INV>(v[4], v[5], v[6], v[7]);  // k1 = 1 -> X[1 + 2 k2]
+  float2 t[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 2; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 2 * k2] = t[4 * k1 + k2];
+}
+
+// 16-point DFT: n = n2 + 4 n1, k = k1 + 4 k2.  Radix-4 over n1, twiddle
+// W16^(n2 k1), radix-4 over n2, then the 4x4 register transpose.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);  // v[n2 + 4 k1]
+  v[5] = twiddle16<INV, 1>(v[5]);
+  v[6] = twiddle16<INV, 2>(v[6]);
+  v[7] = twiddle16<INV, 3>(v[7]);
+  v[9] = twiddle16<INV, 2>(v[9]);
+  v[10] = twiddle16<INV, 4>(v[10]);
+  v[11] = twiddle16<INV, 6>(v[11]);
+  v[13] = twiddle16<INV, 3>(v[13]);
+  v[14] = twiddle16<INV, 6>(v[14]);
+  v[15] = twiddle16<INV, 9>(v[15]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  float2 t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_r(float2 (&u)[R]) {
+  if constexpr (R == 2) dft2<INV>(u[0], u[1]);
+  else if constexpr (R == 4) dft4<INV>(u[0], u[1], u[2], u[3]);
+  else if constexpr (R == 8) dft8<INV>(u);
+  else dft16<INV>(u);
+}
+
+// Padded shared-memory index (one spare slot every 16 elements).
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+template <int N>
+struct FftShape {
+  static constexpr int smem_elems = N + N / 16;
+};
+
+// Radix of the pass with sub-transform size NS: 16 while 16 divides what is
+// left of N, then the remainder (2, 4 or 8).
+template <int N, int NS>
+struct PassRadix {
+  static constexpr int rem = N / NS;
+  static constexpr int value = rem >= 16 ? 16 : rem;
+};
+
+// One butterfly set of a pass (thread-local), twiddled and transformed.
+// Inputs/outputs in v[q + Q s] as described at the top of the file.
+template <int N, int E, int R, int NS, bool INV>
+__device__ __forceinline__ void pass_compute(float2 (&v)[E], int j) {
+  constexpr int T = N / E;
+  constexpr int Q = E / R;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float2 u[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) u[s] = v[q + Q * s];
+    if constexpr (NS > 1) {
+      const int J = j + T * q;
+      const int k = J & (NS - 1);
+      constexpr float scale = (INV ? 2.f : -2.f) / float(NS * R);
+      float sn, cs;
+      sincospif(scale * float(k), &sn, &cs);
+      const float2 w = make_float2(cs, sn);
+      float2 wp = w;
+#pragma unroll
+      for (int s = 1; s < R; ++s) {
+        u[s] = c_mul(u[s], wp);
+        if (s + 1 < R) wp = c_mul(wp, w);
+      }
+    }
+    dft_r<R, INV>(u);
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[q + Q * t] = u[t];
+  }
+}
+
+// Scatter the pass outputs to shared memory at their Stockham positions.
+template <int N, int E, int R, int NS>
+__device__ __forceinline__ void pass_store(const float2 (&v)[E], int j, float2* __restrict__ buf) {
+  constexpr int T = N / E;
+  constexpr int Q = E / R;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int J = j + T * q;
+    const int k = J & (NS - 1);
+    const int base = (J / NS) * NS * R + k;
+#pragma unroll
+    for (int t = 0; t < R; ++t) buf[pad16(base + t * NS)] = v[q + Q * t];
+  }
+}
+
+template <int N, int E>
+__device__ __forceinline__ void gather_regs(float2 (&v)[E], int j, const float2* __restrict__ buf) {
+  constexpr int T = N / E;
+#pragma unroll
+  for (int r = 0; r < E; ++r) v[r] = buf[pad16(j + T * r)];
+}
+
+template <int N, int E>
+__device__ __forceinline__ void scatter_regs(const float2 (&v)[E], int j, float2* __restrict__ buf) {
+  constexpr int T = N / E;
+#pragma unroll
+  for (int r = 0; r < E; ++r) buf[pad16(j + T * r)] = v[r];
+}
+
+// Whole transform.  On entry and exit thread j holds x[j + T r] in v[r].
+// Shared-memory exchanges alternate between buf0 and buf1 when DOUBLE_BUF
+// (one barrier per exchange); with a single buffer a second barrier guards
+// the reuse.  'phase' carries the alternation across calls so that
+// back-to-back transforms in one CTA never overwrite a buffer still being
+// read.  Every thread of the CTA must call this.
+template <int N, int E, bool INV, bool DOUBLE_BUF, int NS = 1>
+__device__ __forceinline__ void fft_block(float2 (&v)[E], int j, float2* buf0, float2* buf1, int& phase) {
+  constexpr int R = PassRadix<N, NS>::value;
+  pass_compute<N, E, R, NS, INV>(v, j);
+  if constexpr (NS * R < N) {
+    float2* buf = (DOUBLE_BUF && phase) ? buf1 : buf0;
+    if constexpr (!DOUBLE_BUF) __syncthreads();
+    pass_store<N, E, R, NS>(v, j, buf);
+    __syncthreads();
+    gather_regs<N, E>(v, j, buf);
+    if constexpr (DOUBLE_BUF) phase ^= 1;
+    fft_block<N, E, INV, DOUBLE_BUF, NS * R>(v, j, buf0, buf1, phase);
+  }
+}
+
+}  // namespace gnss

@@ -1,0 +1,87 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point that include/*.h declares, rejects bad descriptors on the host, and
+shares no code with the oracle."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1309_0052_b300 import build as b
+    b.build()
+    import paper_1309_0052_b300 as g
+    return g
+
+
+def _declared():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        names += re.findall(r"^GNSS_API\s+[\w\s\*]+?\b(gnss_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("gnss_plan_create", "gnss_plan_destroy", "gnss_acquire", "gnss_acquire_device",
+                 "gnss_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib.lib, name), name
+
+
+def test_internal_symbols_are_hidden(lib):
+    # only the C ABI is exported (the library is built with -fvisibility=hidden)
+    with pytest.raises(AttributeError):
+        getattr(lib.lib, "_ZN4gnss9set_errorERKNSt7__cxx1112basic_stringIcSt11char_traitsIcESaIcEEE")
+
+
+@pytest.mark.parametrize("field,value", [("fs_hz", 4095000), ("fs_hz", 3000000), ("fs_hz", 128000),
+                                         ("fs_hz", 32768000), ("coh_ms", 0), ("n_dopp", 0),
+                                         ("prn_mask", 0), ("prn_mask", 1 << 32), ("format", 7),
+                                         ("flags", 0x80), ("dopp_step_hz", 0)])
+def test_bad_descriptor_rejected_on_host(lib, field, value):
+    d = lib.PlanDesc(fs_hz=2048000, coh_ms=1, noncoh=0, dopp_min_hz=-5000, dopp_step_hz=500, n_dopp=21,
+                     prn_mask=0xFFFFFFFF, threshold=2.0, flags=0, format=0)
+    setattr(d, field, value)
+    h = C.c_void_p()
+    st = lib.lib.gnss_plan_create(C.byref(d), C.byref(h))
+    assert st == lib.EINVAL
+    assert not h.value
+    assert lib.lib.gnss_last_error()
+
+
+def test_recording_bytes(lib):
+    assert lib.recording_bytes(lib.FMT_I8_IQ, 8192) == 16384
+    assert lib.recording_bytes(lib.FMT_2BIT_IQ, 409600) == 204800
+    assert lib.recording_bytes(lib.FMT_2BIT_IQ, 3) == 2
+
+
+def test_null_arguments_rejected(lib):
+    h = C.c_void_p()
+    assert lib.lib.gnss_plan_create(None, C.byref(h)) == lib.EINVAL
+    assert lib.lib.gnss_plan_destroy(None) == lib.OK
+    assert lib.lib.gnss_acquire(None, None, 0, 0, None, None, None) == lib.EINVAL
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    """The oracle (test infrastructure) and the product share no source: no
+    include, import or file reference crosses between them."""
+    pkg = os.path.join(ROOT, "paper_1309_0052_b300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            src = open(path).read()
+            assert "import oracle" not in src and "from oracle" not in src and "oracle.c" not in src and "liboracle" not in src, path
+    for path in glob.glob(os.path.join(ROOT, "oracle", "*.*")):
+        if path.endswith((".py", ".c", ".h")):
+            src = open(path).read()
+            assert "paper_1309_0052_b300" not in src and "gnss.h" not in src and "csrc" not in src, path
