@@ -28,7 +28,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -63,58 +62,103 @@ def _flops_total(P, D, B, N, coh):
     return D * B * (8 * coh * N + 5 * N * int(np.log2(N))) + _flops_xcorr(P, D, B, N)
 
 
+class _Nvml:
+    """Read-only NVML queries through the driver's libnvidia-ml (ctypes)."""
+
+    def __init__(self):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        rc = self.lib.nvmlInit_v2()
+        if rc != 0:
+            raise RuntimeError("nvmlInit_v2 returned %d" % rc)
+
+    def handle(self, idx):
+        h = self.C.c_void_p()
+        rc = self.lib.nvmlDeviceGetHandleByIndex_v2(self.C.c_uint(idx), self.C.byref(h))
+        if rc != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex_v2 returned %d" % rc)
+        return h
+
+    def _clock(self, fn, h):
+        v = self.C.c_uint()
+        rc = fn(h, self.C.c_int(1), self.C.byref(v))  # NVML_CLOCK_SM = 1
+        if rc != 0:
+            raise RuntimeError("NVML clock query returned %d" % rc)
+        return v.value
+
+    def sm_clock(self, h):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo, h)
+
+    def max_sm_clock(self, h):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo, h)
+
+    def event_reasons(self, h):
+        v = self.C.c_ulonglong()
+        rc = self.lib.nvmlDeviceGetCurrentClocksEventReasons(h, self.C.byref(v))
+        if rc != 0:
+            raise RuntimeError("nvmlDeviceGetCurrentClocksEventReasons returned %d" % rc)
+        return v.value
+
+
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+    """SM clock and clock-event (throttle) reasons sampled every 5 ms through
+    NVML in a background thread while the timed region runs (read-only)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4}
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_s: float = 0.005):
         self.gpu = gpu_index
-        self.rows = []
-        self.proc = None
-        self.thread = None
+        self.period = period_s
+        self.sm = []
+        self.reasons = set()
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
+        self.error = None
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
+            self._nv = _Nvml()
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            idx = self.gpu
+            if vis:
+                try:
+                    idx = int(vis.split(",")[self.gpu])
+                except ValueError:
+                    idx = self.gpu
+            self._h = self._nv.handle(idx)
+            self.max_mhz = float(self._nv.max_sm_clock(self._h))
+        except Exception as e:  # no NVML: report no samples
+            self.error = repr(e)
             return
-        self.thread = threading.Thread(target=self._read, daemon=True)
-        self.thread.start()
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.rows.append([v.strip() for v in line.split(",")])
+    def _run(self):
+        nv = self._nv
+        while not self._stop.is_set():
+            try:
+                self.sm.append(float(nv.sm_clock(self._h)))
+                r = nv.event_reasons(self._h)
+                for name, bit in self.REASONS.items():
+                    if r & bit:
+                        self.reasons.add(name)
+            except Exception as e:
+                self.error = repr(e)
+                return
+            time.sleep(self.period)
 
     def stop(self):
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-        if self.thread is not None:
-            self.thread.join(timeout=5)
-        sm = []
-        mx = None
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            try:
-                sm.append(float(r[1]))
-                mx = float(r[2])
-                for k, nm in enumerate(names):
-                    if r[4 + k].lower() == "active":
-                        reasons.add(nm)
-            except (ValueError, IndexError):
-                continue
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        self._stop.set()
+        if self._thread is not None:
+            self._thread.join(timeout=2)
+        out = {"sm_mhz": statistics.median(self.sm) if self.sm else None, "sm_max_mhz": self.max_mhz,
+               "reasons": sorted(self.reasons), "samples": len(self.sm), "source": "nvml (libnvidia-ml)"}
+        if self.error:
+            out["error"] = self.error
+        return out
 
 
 def _dist():
@@ -308,8 +352,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
