@@ -190,6 +190,32 @@ GNSS_API gnss_status gnss_acquire(gnss_plan* plan, const void* samples, size_t n
 GNSS_API gnss_status gnss_acquire_device(gnss_plan* plan, const void* samples_dev, size_t n_samples,
                                 gnss_detection* out_dev, float* surface_dev, void* stream);
 
+/* Acquisition that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at
+ * request time -- services that must keep a fixed device footprint after
+ * start-up, or processes where another allocator (a framework's caching
+ * allocator, a reserved arena) owns the device memory, so that cudaMalloc or
+ * cudaMallocAsync is forbidden or may fail.  It computes exactly what
+ * gnss_acquire_device computes, with the same kernels, but takes its scratch
+ * (n_dopp * blocks * N * 8 bytes of spectra plus the per-row statistics)
+ * from one fixed 32 MiB device array inside the library, which every GPU
+ * that loads the library holds until the process exits.
+ *  - Inputs and outputs are the caller's, as in gnss_acquire_device:
+ *    samples_dev (16-byte aligned), out_dev (n_prn records), surface_dev
+ *    (NULL or [n_sets][n_prn][n_dopp][N]).  Calls no cudaMalloc, cudaFree or
+ *    other allocating routine.
+ *  - A request whose scratch exceeds 32 MiB is rejected with GNSS_EINVAL and
+ *    a message giving the bytes it needs; nothing is launched.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array and it keeps the last call's
+ *    contents (every value a call reads is written by that call first).
+ *    Calls whose work overlaps on the GPU (other streams, or other threads)
+ *    race on it: serialise them, e.g. on one stream. */
+GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                          gnss_detection* out_dev, float* surface_dev, void* stream);
+
 /* Stage entry points (one launch each) for stage-level checks and for the
  * one-stage-per-launch comparison.
  * gnss_stage_wipe_fft: carrier wipe-off, coherent fold and forward FFT of
