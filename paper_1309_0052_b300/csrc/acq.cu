@@ -54,7 +54,7 @@ template <int N>
 struct Cfg {
   static constexpr int E = N >= 16384 ? 32 : 16;
   static constexpr int T = N / E;
-  static constexpr bool CREG = (E == 16);                       // code spectrum kept in registers
+  static constexpr bool TWC = (E == 16);                        // twiddle bases cached in registers
   static constexpr size_t buf_bytes = sizeof(float2) * FftShape<N>::smem_elems;
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
   static constexpr size_t smem = (DB ? 2 : 1) * buf_bytes;
@@ -207,8 +207,11 @@ __global__ void __launch_bounds__(Cfg<N>::T) k_wipe_fft(const uint8_t* __restric
     car = c_mul(car, step);
   }
   // transpose m = E j + e  ->  register layout j + T r
+  {
+    float2* b = buf0 + pad16(E * j);  // E j is a multiple of 16
 #pragma unroll
-  for (int e = 0; e < E; ++e) buf0[pad16(E * j + e)] = v[e];
+    for (int e = 0; e < E; ++e) b[e + (e >> 4)] = v[e];
+  }
   __syncthreads();
   gather_regs<N, E>(v, j, buf0);
   int phase = 1;  // next exchange uses buf1 (buf0 may still be read by a slower thread)
@@ -314,20 +317,32 @@ __device__ __forceinline__ void row_stats(const float (&a)[E], int j, int excl, 
 // K4: correlate.  One CTA per (PRN p, Doppler d), tile = d * P + p; loops
 // over the B blocks of Y[d], accumulating |R|^2 per set in registers.
 // ---------------------------------------------------------------------------
-template <int N, int E, bool INV, bool DB>
-__device__ __forceinline__ void corr_block(const float2* __restrict__ y, const float2 (&c)[E],
-                                           const float2* __restrict__ cglob, int j, float2* buf0, float2* buf1,
-                                           int& phase, float (&acc)[E]) {
+// One block: Y * conj(C_p) -> IFFT -> |.|^2 added to acc0 (even blocks) or,
+// with half-bit sets, to acc1 (odd blocks); one loop body serves both sets.
+template <int N, int E, bool DB, bool TWC, bool HALF>
+__device__ __forceinline__ void corr_block(const float2* __restrict__ y, const float2* __restrict__ cp, int j,
+                                           float2* buf0, float2* buf1, int& phase, FftTw<N, E, true>& tw,
+                                           float (&acc0)[E], float (&acc1)[E], bool odd) {
   constexpr int T = N / E;
+  if constexpr (TWC) tw.launder();
+  // Re-read the code spectrum from L1 every block: hoisting these 16 loads
+  // out of the block loop would pin 32 registers and force spills.
+  asm volatile("" : "+l"(cp));
   float2 v[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) {
-    const float2 cv = (cglob != nullptr) ? __ldg(cglob + j + T * r) : c[r];
-    v[r] = c_mulconj(__ldg(y + j + T * r), cv);
+    // Y streams from L2 (not kept in L1); the code spectrum stays L1-resident
+    v[r] = c_mulconj(__ldcg(y + j + T * r), __ldg(cp + j + T * r));
   }
-  fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
+  if constexpr (TWC) fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw);
+  else fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
+  if (HALF && odd) {  // uniform across the CTA
 #pragma unroll
-  for (int r = 0; r < E; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
+    for (int r = 0; r < E; ++r) acc1[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc1[r]));
+  } else {
+#pragma unroll
+    for (int r = 0; r < E; ++r) acc0[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc0[r]));
+  }
 }
 
 template <int N, bool HALF>
@@ -335,7 +350,7 @@ __global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB)
     k_xcorr(const float2* __restrict__ Y, const float2* __restrict__ cspec, int B, int D, int P, int excl,
             float* __restrict__ surface, RowStat* __restrict__ rows) {
   constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
-  constexpr bool DB = Cfg<N>::DB;
+  constexpr bool DB = Cfg<N>::DB, TWC = Cfg<N>::TWC;
   extern __shared__ float2 sm[];
   float2* buf0 = sm;
   float2* buf1 = DB ? sm + FftShape<N>::smem_elems : sm;
@@ -344,29 +359,15 @@ __global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB)
   const int j = threadIdx.x;
   const int p = blockIdx.x % P, d = blockIdx.x / P;
   const float2* cp = cspec + (size_t)p * N;
-  float2 c[E];
-  const float2* cglob = nullptr;
-  if constexpr (Cfg<N>::CREG) {
-#pragma unroll
-    for (int r = 0; r < E; ++r) c[r] = __ldg(cp + j + T * r);
-  } else {
-    cglob = cp;
-#pragma unroll
-    for (int r = 0; r < E; ++r) c[r] = make_float2(0.f, 0.f);
-  }
+  FftTw<N, E, true> tw;
+  if constexpr (TWC) tw.init(j);
   float acc0[E], acc1[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) acc0[r] = acc1[r] = 0.f;
   const float2* yd = Y + (size_t)d * B * N;
   int phase = 0;
-  if constexpr (HALF) {
-    for (int b = 0; b < B; b += 2) {
-      corr_block<N, E, true, DB>(yd + (size_t)b * N, c, cglob, j, buf0, buf1, phase, acc0);
-      if (b + 1 < B) corr_block<N, E, true, DB>(yd + (size_t)(b + 1) * N, c, cglob, j, buf0, buf1, phase, acc1);
-    }
-  } else {
-    for (int b = 0; b < B; ++b) corr_block<N, E, true, DB>(yd + (size_t)b * N, c, cglob, j, buf0, buf1, phase, acc0);
-  }
+  for (int b = 0; b < B; ++b)
+    corr_block<N, E, DB, TWC, HALF>(yd + (size_t)b * N, cp, j, buf0, buf1, phase, tw, acc0, acc1, (b & 1) != 0);
   // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
   constexpr float sc = 1.f / ((float)N * (float)N);
 #pragma unroll

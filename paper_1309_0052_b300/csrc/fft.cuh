@@ -184,32 +184,43 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[E], int j) {
 }
 
 // Scatter the pass outputs to shared memory at their Stockham positions.
+// NS is 1 or a multiple of 16 (radix-16 passes come first), and for NS = 1
+// base = R J keeps base mod 16 + t < 16; either way
+// pad16(base + t NS) = pad16(base) + t NS + (t NS) / 16, so each store is one
+// per-butterfly address plus a compile-time offset.
 template <int N, int E, int R, int NS>
 __device__ __forceinline__ void pass_store(const float2 (&v)[E], int j, float2* __restrict__ buf) {
+  static_assert(NS == 1 || NS % 16 == 0, "pass order: radix-16 passes first");
   constexpr int T = N / E;
   constexpr int Q = E / R;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int J = j + T * q;
     const int k = J & (NS - 1);
-    const int base = (J / NS) * NS * R + k;
+    float2* b = buf + pad16((J / NS) * NS * R + k);
 #pragma unroll
-    for (int t = 0; t < R; ++t) buf[pad16(base + t * NS)] = v[q + Q * t];
+    for (int t = 0; t < R; ++t) b[t * NS + ((t * NS) >> 4)] = v[q + Q * t];
   }
 }
 
+// Element j + T r of the padded buffer; T is a multiple of 16, so the offset
+// from pad16(j) is the compile-time T r + T r / 16.
 template <int N, int E>
 __device__ __forceinline__ void gather_regs(float2 (&v)[E], int j, const float2* __restrict__ buf) {
   constexpr int T = N / E;
+  static_assert(T % 16 == 0, "T must be a multiple of 16");
+  const float2* b = buf + pad16(j);
 #pragma unroll
-  for (int r = 0; r < E; ++r) v[r] = buf[pad16(j + T * r)];
+  for (int r = 0; r < E; ++r) v[r] = b[T * r + ((T * r) >> 4)];
 }
 
 template <int N, int E>
 __device__ __forceinline__ void scatter_regs(const float2 (&v)[E], int j, float2* __restrict__ buf) {
   constexpr int T = N / E;
+  static_assert(T % 16 == 0, "T must be a multiple of 16");
+  float2* b = buf + pad16(j);
 #pragma unroll
-  for (int r = 0; r < E; ++r) buf[pad16(j + T * r)] = v[r];
+  for (int r = 0; r < E; ++r) b[T * r + ((T * r) >> 4)] = v[r];
 }
 
 // Whole transform.  On entry and exit thread j holds x[j + T r] in v[r].
@@ -230,6 +241,133 @@ __device__ __forceinline__ void fft_block(float2 (&v)[E], int j, float2* buf0, f
     gather_regs<N, E>(v, j, buf);
     if constexpr (DOUBLE_BUF) phase ^= 1;
     fft_block<N, E, INV, DOUBLE_BUF, NS * R>(v, j, buf0, buf1, phase);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Twiddle bases held across many transforms of one CTA.
+//
+// A pass with sub-transform size NS > 1 multiplies input s (1 <= s < R) by
+// W^(s k), W = exp(-+2 pi i / (NS R)), k = J mod NS.  Writing s = 4 hi + lo,
+// W^(s k) = W^(lo k) W^(4 hi k), so a thread keeps a[] = W^k, W^2k, W^3k and
+// b[] = W^4k, W^8k, ... and forms each twiddle with at most one complex
+// multiply.  These bases depend only on the thread, not on the data, so a
+// kernel that runs many transforms computes them once.
+// ---------------------------------------------------------------------------
+template <int R>
+struct TwBase {
+  static constexpr int NA = R >= 4 ? 3 : 1;
+  static constexpr int NB = R >= 8 ? R / 4 - 1 : 0;
+  float2 a[NA];
+  float2 b[NB > 0 ? NB : 1];
+
+  __device__ __forceinline__ void init(float turns2) {  // W^k = exp(i pi turns2)
+    float sn, cs;
+    sincospif(turns2, &sn, &cs);
+    a[0] = make_float2(cs, sn);
+    if constexpr (NA > 1) {
+      a[1] = c_mul(a[0], a[0]);
+      a[2] = c_mul(a[1], a[0]);
+    }
+    if constexpr (NB > 0) {
+      const float2 w4 = c_mul(a[1], a[1]);
+      b[0] = w4;
+#pragma unroll
+      for (int i = 1; i < NB; ++i) b[i] = c_mul(b[i - 1], w4);
+    }
+  }
+
+  // Make the bases opaque to the optimiser for one loop iteration, so that the
+  // twiddles formed from them are recomputed next to their use instead of
+  // being hoisted out of the caller's loop into extra registers.
+  __device__ __forceinline__ void launder() {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) asm volatile("" : "+f"(a[i].x), "+f"(a[i].y));
+    if constexpr (NB > 0) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i) asm volatile("" : "+f"(b[i].x), "+f"(b[i].y));
+    }
+  }
+
+  template <int S>
+  __device__ __forceinline__ float2 get() const {
+    constexpr int lo = S & 3, hi = S >> 2;
+    if constexpr (hi == 0) return a[lo - 1];
+    else if constexpr (lo == 0) return b[hi - 1];
+    else return c_mul(a[lo - 1], b[hi - 1]);
+  }
+};
+
+template <int R, int S, bool LAST>
+struct TwApply {
+  __device__ __forceinline__ static void run(float2 (&u)[R], const TwBase<R>& t) {
+    u[S] = c_mul(u[S], t.template get<S>());
+    if constexpr (!LAST) TwApply<R, S + 1, S + 2 == R>::run(u, t);
+  }
+};
+
+// Twiddle bases of every pass of an N-point transform for thread j.
+template <int N, int E, bool INV, int NS = 1>
+struct FftTw {
+  static constexpr int R = PassRadix<N, NS>::value;
+  static constexpr int Q = E / R;
+  static constexpr int T = N / E;
+  TwBase<R> tw[NS > 1 ? Q : 1];
+  FftTw<N, E, INV, NS * R> next;
+
+  __device__ __forceinline__ void init(int j) {
+    if constexpr (NS > 1) {
+      constexpr float scale = (INV ? 2.f : -2.f) / float(NS * R);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) tw[q].init(scale * float((j + T * q) & (NS - 1)));
+    }
+    next.init(j);
+  }
+
+  __device__ __forceinline__ void launder() {
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) tw[q].launder();
+    }
+    next.launder();
+  }
+};
+
+template <int N, int E, bool INV>
+struct FftTw<N, E, INV, N> {
+  __device__ __forceinline__ void init(int) {}
+  __device__ __forceinline__ void launder() {}
+};
+
+template <int N, int E, int R, int NS, bool INV>
+__device__ __forceinline__ void pass_compute_tw(float2 (&v)[E], const FftTw<N, E, INV, NS>& tw) {
+  constexpr int Q = E / R;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float2 u[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) u[s] = v[q + Q * s];
+    if constexpr (NS > 1) TwApply<R, 1, R == 2>::run(u, tw.tw[q]);
+    dft_r<R, INV>(u);
+#pragma unroll
+    for (int t = 0; t < R; ++t) v[q + Q * t] = u[t];
+  }
+}
+
+// fft_block with the twiddle bases precomputed in 'tw' (see FftTw).
+template <int N, int E, bool INV, bool DOUBLE_BUF, int NS = 1>
+__device__ __forceinline__ void fft_block_tw(float2 (&v)[E], int j, float2* buf0, float2* buf1, int& phase,
+                                             const FftTw<N, E, INV, NS>& tw) {
+  constexpr int R = PassRadix<N, NS>::value;
+  pass_compute_tw<N, E, R, NS, INV>(v, tw);
+  if constexpr (NS * R < N) {
+    float2* buf = (DOUBLE_BUF && phase) ? buf1 : buf0;
+    if constexpr (!DOUBLE_BUF) __syncthreads();
+    pass_store<N, E, R, NS>(v, j, buf);
+    __syncthreads();
+    gather_regs<N, E>(v, j, buf);
+    if constexpr (DOUBLE_BUF) phase ^= 1;
+    fft_block_tw<N, E, INV, DOUBLE_BUF, NS * R>(v, j, buf0, buf1, phase, tw.next);
   }
 }
 

@@ -6,7 +6,7 @@
 
 #include <string>
 
-#include "../../include/gnss.h"
+#include "gnss.h"
 
 namespace gnss {
 
