@@ -285,14 +285,27 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def _kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("fft.cuh", "acq.cu"):
+        with open(os.path.join(ROOT, "paper_1309_0052_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _load_traffic():
-    """DRAM bytes per correlate launch from the committed ncu summary, or None."""
+    """DRAM bytes per correlate launch from the committed ncu summary; None when
+    there is none or when the kernel source changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "traffic_k_xcorr_weak_100ms.json")
     try:
         with open(path) as fh:
-            return json.load(fh).get("dram_bytes_per_launch")
+            rec = json.load(fh)
     except (OSError, ValueError):
         return None
+    if rec.get("source_hash") != _kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def _oracle_sample(rec, threads):
