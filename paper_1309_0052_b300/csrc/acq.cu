@@ -2,12 +2,14 @@
 //
 //   k_gold         G1/G2 LFSR Gold codes (code NCO input), bit-exact
 //   k_code_spectra replica sampling at fs + forward FFT -> resident C_p
-//   k_wipe_fft     2-bit / int8 I/Q unpack, carrier wipe-off, coherent fold
-//                  of T_coh ms, forward FFT: Y_{f,b}     (first mixing + FFT)
+//   k_fold         2-bit / int8 I/Q unpack and coherent fold of T_coh ms with
+//                  the per-millisecond carrier factor, once per group of
+//                  Doppler bins sharing f mod 1000          (first mixing)
+//   k_carrier_fft  per-bin carrier wipe-off + forward FFT: Y_{f,b}
 //   k_xcorr        Y * conj(C_p), IFFT, |.|^2, non-coherent accumulation over
-//                  blocks in registers, per-row peak statistics
-//                                                   (second mixing + IFFT)
-//   k_peak         per-PRN peak / second peak / ratio (signal detection)
+//                  blocks in registers, per-row peak statistics, and in the
+//                  last CTA of each PRN the peak / second peak / ratio
+//                  detection                  (second mixing + IFFT + detection)
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -91,13 +93,12 @@ __global__ void __launch_bounds__(Cfg<N>::T) k_code_spectra(const int8_t* __rest
 // With n = bL + iN + m the wipe-off phase splits exactly as
 //   f n / fs = f (bL + m) / fs + f i / 1000        (N / fs = 1 ms),
 // so y[m] = exp(-j 2 pi ((f (bL+m)) mod fs)/fs) * sum_i x[n] w_i with the
-// per-millisecond constant w_i = exp(-j 2 pi ((f i) mod 1000) / 1000).  Each
-// thread folds E consecutive samples m = E j + e (vector loads: 8 or 16 bytes
-// of 2-bit data, 32 or 64 bytes of int8 per millisecond), computes the
-// carrier of its first sample from the exact integer phase and steps it by
-// the per-sample rotation, then the block is transposed through shared
-// memory into the FFT's register layout.
-// Grid: one CTA per (Doppler d, block b), tile = d * B + b.
+// per-millisecond constant w_i = exp(-j 2 pi ((f i) mod 1000) / 1000), which
+// depends on f only through f mod 1000.  The fold sum is therefore computed
+// once per group of bins with the same f mod 1000 (k_fold; vector loads of
+// 8 or 16 bytes of 2-bit data, 32 or 64 bytes of int8 per thread and
+// millisecond), and each bin applies only its own carrier before the FFT
+// (k_carrier_fft).
 // ---------------------------------------------------------------------------
 template <int E, int FMT>
 __device__ __forceinline__ void load_ms(const uint8_t* __restrict__ base, int64_t n0, float (&xi)[E],
@@ -106,7 +107,9 @@ __device__ __forceinline__ void load_ms(const uint8_t* __restrict__ base, int64_
     // E samples = E/2 bytes; sample e: bits [4e, 4e+4) of the little-endian words
     const uint32_t* w = reinterpret_cast<const uint32_t*>(base + n0 / 2);
     uint32_t words[E / 8];
-    if constexpr (E == 16) {
+    if constexpr (E == 8) {
+      words[0] = __ldg(w);
+    } else if constexpr (E == 16) {
       const uint2 t = __ldg(reinterpret_cast<const uint2*>(w));
       words[0] = t.x;
       words[1] = t.y;
@@ -143,28 +146,39 @@ __device__ __forceinline__ void load_ms(const uint8_t* __restrict__ base, int64_
   }
 }
 
-template <int N, int FMT>
-__global__ void __launch_bounds__(Cfg<N>::T) k_wipe_fft(const uint8_t* __restrict__ samples, int fs, int coh,
-                                                       int B, int dopp_min, int dopp_step,
-                                                       float2* __restrict__ Y) {
-  constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
-  extern __shared__ float2 sm[];
-  float2* buf0 = sm;
-  float2* buf1 = Cfg<N>::DB ? sm + FftShape<N>::smem_elems : sm;
-  const int j = threadIdx.x;
-  const int d = blockIdx.x / B, b = blockIdx.x % B;
-  const int f = dopp_min + d * dopp_step;
-  const int64_t L = (int64_t)coh * N;
-  const int64_t n_first = (int64_t)b * L + (int64_t)E * j;  // first sample of this thread, ms 0
+// k_fold: z_g[m] = sum_i x[bL + iN + m] w_i for every fold group g and block b,
+// with w_i = exp(-j 2 pi ((rho_g i) mod 1000) / 1000), rho_g = f mod 1000 of
+// the Doppler bins of the group (all bins share one group when T_coh = 1).
+// Each thread folds 8 consecutive samples (one 4-byte load of 2-bit data or
+// one 16-byte load of int8 per millisecond); FoldCfg<N>::CPB CTAs of
+// FoldCfg<N>::T threads cover one (g, b).  Output in natural order.  CTA 0
+// also clears the per-PRN completion counters of k_xcorr.
+template <int N>
+struct FoldCfg {
+  static constexpr int E = 8;
+  static constexpr int T = N / E < 128 ? N / E : 128;
+  static constexpr int CPB = N / (E * T);  // CTAs per (group, block)
+};
 
-  // fold: acc[e] = sum_i x[n_first + iN + e] w_i
+template <int N, int FMT>
+__global__ void __launch_bounds__(FoldCfg<N>::T) k_fold(const uint8_t* __restrict__ samples, int coh, int B,
+                                                       const int* __restrict__ gkey, float2* __restrict__ Z,
+                                                       unsigned* __restrict__ counters, int P) {
+  constexpr int E = FoldCfg<N>::E, T = FoldCfg<N>::T, CPB = FoldCfg<N>::CPB;
+  const int gb = blockIdx.x / CPB;             // g * B + b
+  const int m0 = E * ((blockIdx.x % CPB) * T + threadIdx.x);
+  const int g = gb / B, b = gb % B;
+  if (counters != nullptr && blockIdx.x == 0)
+    for (int p = threadIdx.x; p < P; p += T) counters[p] = 0u;
+  const int rho = gkey[g];
+  const int64_t n_first = (int64_t)b * coh * N + m0;  // first sample of this thread, ms 0
   float ar[E], ai[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) ar[e] = ai[e] = 0.f;
   float wsum_r = 0.f, wsum_i = 0.f;
-  const int f1000 = ((f % 1000) + 1000) % 1000;
+#pragma unroll 5
   for (int i = 0; i < coh; ++i) {
-    const int ri = (int)(((int64_t)f1000 * i) % 1000);
+    const int ri = (int)(((int64_t)rho * i) % 1000);
     float ws, wc;
     sincospif(-2.f * (float)ri / 1000.f, &ws, &wc);
     float xi[E], xq[E];
@@ -191,31 +205,44 @@ __global__ void __launch_bounds__(Cfg<N>::T) k_wipe_fft(const uint8_t* __restric
       ai[e] = fmaf(-3.f, wsum_r + wsum_i, ai[e]);
     }
   }
-  // carrier of sample bL + E j + e: exact integer phase for e = 0, then steps
+  float4* out = reinterpret_cast<float4*>(Z + ((size_t)gb * N + m0));
+#pragma unroll
+  for (int e = 0; e < E; e += 2) out[e / 2] = make_float4(ar[e], ai[e], ar[e + 1], ai[e + 1]);
+}
+
+// k_carrier_fft: one CTA per (Doppler d, block b), tile = d * B + b.  Loads the
+// folded block of its group in the FFT's register layout (m = j + T r),
+// multiplies by the carrier exp(-j 2 pi ((f (bL + m)) mod fs) / fs) -- exact
+// integer phase for r = 0, then a rotation by T samples per r -- and runs
+// the forward FFT: Y_{f,b} = FFT_N(y_{f,b}).
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::T) k_carrier_fft(const float2* __restrict__ Z, int fs, int coh, int B,
+                                                          int dopp_min, int dopp_step,
+                                                          const int* __restrict__ group, float2* __restrict__ Y) {
+  constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
+  extern __shared__ float2 sm[];
+  float2* buf0 = sm;
+  float2* buf1 = Cfg<N>::DB ? sm + FftShape<N>::smem_elems : sm;
+  const int j = threadIdx.x;
+  const int d = blockIdx.x / B, b = blockIdx.x % B;
+  const int f = dopp_min + d * dopp_step;
+  const float2* z = Z + ((size_t)group[d] * B + b) * N;
   const int64_t fr = (((int64_t)f % fs) + fs) % fs;
-  const int64_t r0 = (fr * (int64_t)((int64_t)b * L + (int64_t)E * j)) % fs;
-  float cs0, cc0, ss, sc;
+  const int64_t r0 = (fr * ((int64_t)b * coh * N + j)) % fs;
+  const int64_t rs = (fr * T) % fs;
   const float inv_fs = 1.f / (float)fs;
-  sincospif(-2.f * (float)r0 * inv_fs, &cs0, &cc0);
-  sincospif(-2.f * (float)fr * inv_fs, &ss, &sc);
-  float2 car = make_float2(cc0, cs0);
+  float s0, c0, ss, sc;
+  sincospif(-2.f * (float)r0 * inv_fs, &s0, &c0);
+  sincospif(-2.f * (float)rs * inv_fs, &ss, &sc);
+  float2 car = make_float2(c0, s0);
   const float2 step = make_float2(sc, ss);
   float2 v[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    v[e] = c_mul(make_float2(ar[e], ai[e]), car);
+  for (int r = 0; r < E; ++r) {
+    v[r] = c_mul(__ldg(z + j + T * r), car);
     car = c_mul(car, step);
   }
-  // transpose m = E j + e  ->  register layout j + T r
-  {
-    float2* b = buf0 + pad16(E * j);  // E j is a multiple of 16
-#pragma unroll
-    for (int e = 0; e < E; ++e) b[e + (e >> 4)] = v[e];
-  }
-  __syncthreads();
-  gather_regs<N, E>(v, j, buf0);
-  int phase = 1;  // next exchange uses buf1 (buf0 may still be read by a slower thread)
-  if constexpr (!Cfg<N>::DB) phase = 0;
+  int phase = 0;
   fft_block<N, E, false, Cfg<N>::DB>(v, j, buf0, buf1, phase);
   float2* out = Y + (size_t)blockIdx.x * N;
 #pragma unroll
@@ -345,10 +372,63 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, const f
   }
 }
 
+// Per-PRN detection, run by the last CTA to finish a PRN (all its threads):
+// best row over the Doppler bins (ties to the smallest bin), its second
+// peak (or, with GNSS_SECOND_WHOLE, the largest surface cell outside the
+// exclusion band around the peak phase), ratio, and the half-bit set with
+// the larger ratio (ties to set 0).  Rows and surface cells written by other
+// CTAs are read through L2.
+template <int N, int T>
+__device__ __forceinline__ void finalize_prn(const XcorrArgs& a, int p, int sets, float* s_val, uint32_t* s_idx) {
+  float best_ratio = -1.f;
+  gnss_detection rec;
+  for (int s = 0; s < sets; ++s) {
+    const RowStat* rs = a.rows + ((size_t)s * a.P + p) * a.D;
+    float v = -1.f;
+    uint32_t db = 0;
+    for (int d = threadIdx.x; d < a.D; d += T) {
+      const float pk = __ldcg(&rs[d].peak);
+      if (pk > v) {
+        v = pk;
+        db = (uint32_t)d;
+      }
+    }
+    block_argmax<T>(v, db, s_val, s_idx);
+    const float4 raw = __ldcg(reinterpret_cast<const float4*>(rs + db));
+    const float peak = raw.x;
+    const uint32_t tau = __float_as_uint(raw.y);
+    float second = raw.z;
+    if (a.second_whole) {
+      const float* S = a.surface + ((size_t)s * a.P + p) * a.D * (size_t)N;
+      float m = 0.f;
+      for (int idx = threadIdx.x; idx < a.D * N; idx += T) {
+        const int t = idx & (N - 1);
+        int dist = abs(t - (int)tau);
+        dist = min(dist, N - dist);
+        if (dist > a.excl) m = fmaxf(m, __ldcg(S + idx));
+      }
+      second = block_max<T>(m, s_val);
+    }
+    const float ratio = second > 0.f ? peak / second : INFINITY;
+    if (s == 0 || ratio > best_ratio) {
+      best_ratio = ratio;
+      rec.prn = (uint8_t)a.prns[p];
+      rec.set = (uint8_t)s;
+      rec.reserved = 0;
+      rec.dopp_bin = (int32_t)db;
+      rec.dopp_hz = a.dopp_min + (int32_t)db * a.dopp_step;
+      rec.code_phase = tau;
+      rec.peak = peak;
+      rec.second = second;
+      rec.ratio = ratio;
+    }
+  }
+  rec.detected = (uint8_t)(best_ratio >= a.threshold);
+  if (threadIdx.x == 0) a.out[p] = rec;
+}
+
 template <int N, bool HALF>
-__global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB)
-    k_xcorr(const float2* __restrict__ Y, const float2* __restrict__ cspec, int B, int D, int P, int excl,
-            float* __restrict__ surface, RowStat* __restrict__ rows) {
+__global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB) k_xcorr(const XcorrArgs a) {
   constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
   constexpr bool DB = Cfg<N>::DB, TWC = Cfg<N>::TWC;
   extern __shared__ float2 sm[];
@@ -356,17 +436,18 @@ __global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB)
   float2* buf1 = DB ? sm + FftShape<N>::smem_elems : sm;
   __shared__ float s_val[32];
   __shared__ uint32_t s_idx[32];
+  __shared__ unsigned s_last;
   const int j = threadIdx.x;
-  const int p = blockIdx.x % P, d = blockIdx.x / P;
-  const float2* cp = cspec + (size_t)p * N;
+  const int p = blockIdx.x % a.P, d = blockIdx.x / a.P;
+  const float2* cp = a.cspec + (size_t)p * N;
   FftTw<N, E, true> tw;
   if constexpr (TWC) tw.init(j);
   float acc0[E], acc1[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) acc0[r] = acc1[r] = 0.f;
-  const float2* yd = Y + (size_t)d * B * N;
+  const float2* yd = a.Y + (size_t)d * a.B * N;
   int phase = 0;
-  for (int b = 0; b < B; ++b)
+  for (int b = 0; b < a.B; ++b)
     corr_block<N, E, DB, TWC, HALF>(yd + (size_t)b * N, cp, j, buf0, buf1, phase, tw, acc0, acc1, (b & 1) != 0);
   // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
   constexpr float sc = 1.f / ((float)N * (float)N);
@@ -378,76 +459,23 @@ __global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB)
   constexpr int sets = HALF ? 2 : 1;
 #pragma unroll
   for (int s = 0; s < sets; ++s) {
-    const float(&a)[E] = (s == 0) ? acc0 : acc1;
-    if (surface != nullptr) {
-      float* row = surface + (((size_t)s * P + p) * D + d) * (size_t)N;
+    const float(&acc)[E] = (s == 0) ? acc0 : acc1;
+    if (a.surface != nullptr) {
+      float* row = a.surface + (((size_t)s * a.P + p) * a.D + d) * (size_t)N;
 #pragma unroll
-      for (int r = 0; r < E; ++r) row[j + T * r] = a[r];
+      for (int r = 0; r < E; ++r) row[j + T * r] = acc[r];
     }
-    row_stats<N, E>(a, j, excl, s_val, s_idx, rows + ((size_t)s * P + p) * D + d);
+    row_stats<N, E>(acc, j, a.excl, s_val, s_idx, a.rows + ((size_t)s * a.P + p) * a.D + d);
   }
-}
-
-// ---------------------------------------------------------------------------
-// K5: per-PRN detection.  One warp per PRN: best row (ties to the smallest
-// Doppler index), ratio = peak / second, set with the larger ratio.
-// With GNSS_SECOND_WHOLE the second peak is searched over the whole stored
-// surface outside the exclusion band around the peak phase.
-// ---------------------------------------------------------------------------
-__global__ void k_peak(const RowStat* __restrict__ rows, const int* __restrict__ prns, const float* __restrict__ surface,
-                       int P, int D, int N, int sets, int excl, int dopp_min, int dopp_step, float threshold,
-                       int second_whole, gnss_detection* __restrict__ out) {
-  const int p = blockIdx.x, lane = threadIdx.x;
-  float best_ratio = -1.f;
-  gnss_detection rec;
-  for (int s = 0; s < sets; ++s) {
-    const RowStat* rs = rows + ((size_t)s * P + p) * D;
-    float v = -1.f;
-    uint32_t dbest = 0;
-    for (int d = lane; d < D; d += 32) {
-      const float pk = rs[d].peak;
-      if (pk > v) {
-        v = pk;
-        dbest = (uint32_t)d;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-      const uint32_t od = __shfl_xor_sync(0xffffffffu, dbest, o);
-      better(v, dbest, ov, od);
-    }
-    const RowStat r = rs[dbest];
-    float second = r.second;
-    if (second_whole) {
-      const float* S = surface + ((size_t)s * P + p) * D * (size_t)N;
-      float m = 0.f;
-      for (size_t idx = lane; idx < (size_t)D * N; idx += 32) {
-        int t = (int)(idx % N);
-        int dist = abs(t - (int)r.tau);
-        dist = min(dist, N - dist);
-        if (dist > excl) m = fmaxf(m, S[idx]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      second = m;
-    }
-    const float ratio = second > 0.f ? r.peak / second : INFINITY;
-    if (s == 0 || ratio > best_ratio) {
-      best_ratio = ratio;
-      rec.prn = (uint8_t)prns[p];
-      rec.set = (uint8_t)s;
-      rec.reserved = 0;
-      rec.dopp_bin = (int32_t)dbest;
-      rec.dopp_hz = dopp_min + (int32_t)dbest * dopp_step;
-      rec.code_phase = r.tau;
-      rec.peak = r.peak;
-      rec.second = second;
-      rec.ratio = ratio;
-    }
+  // The last CTA of PRN p (of its D Doppler rows) runs the detection.
+  __threadfence();
+  __syncthreads();
+  if (j == 0) s_last = (atomicAdd(a.counters + p, 1u) == (unsigned)(a.D - 1)) ? 1u : 0u;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    finalize_prn<N, T>(a, p, sets, s_val, s_idx);
   }
-  rec.detected = (uint8_t)(best_ratio >= threshold);
-  if (lane == 0) out[p] = rec;
 }
 
 // ---------------------------------------------------------------------------
@@ -492,54 +520,75 @@ cudaError_t launch_code_spectra(const int8_t* d_codes, int P, int N, float2* d_c
 }
 
 template <int N>
-static cudaError_t wipe_fft_n(const AcqShape& s, const uint8_t* d_samples, float2* d_Y, cudaStream_t stream) {
-  const int grid = s.D * s.B;
-  if (s.format == GNSS_FMT_2BIT_IQ) {
-    cudaError_t e = set_smem(k_wipe_fft<N, GNSS_FMT_2BIT_IQ>, Cfg<N>::smem);
-    if (e != cudaSuccess) return e;
-    k_wipe_fft<N, GNSS_FMT_2BIT_IQ><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(d_samples, s.fs, s.coh, s.B,
-                                                                             s.dopp_min, s.dopp_step, d_Y);
-  } else {
-    cudaError_t e = set_smem(k_wipe_fft<N, GNSS_FMT_I8_IQ>, Cfg<N>::smem);
-    if (e != cudaSuccess) return e;
-    k_wipe_fft<N, GNSS_FMT_I8_IQ><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(d_samples, s.fs, s.coh, s.B,
-                                                                           s.dopp_min, s.dopp_step, d_Y);
-  }
+static cudaError_t wipe_fft_n(const AcqShape& s, const uint8_t* d_samples, const int* d_group, const int* d_gkey,
+                              float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream) {
+  const int fgrid = s.G * s.B * FoldCfg<N>::CPB;
+  if (s.format == GNSS_FMT_2BIT_IQ)
+    k_fold<N, GNSS_FMT_2BIT_IQ><<<fgrid, FoldCfg<N>::T, 0, stream>>>(d_samples, s.coh, s.B, d_gkey, d_Z, d_counters,
+                                                                     s.P);
+  else
+    k_fold<N, GNSS_FMT_I8_IQ><<<fgrid, FoldCfg<N>::T, 0, stream>>>(d_samples, s.coh, s.B, d_gkey, d_Z, d_counters,
+                                                                   s.P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = set_smem(k_carrier_fft<N>, Cfg<N>::smem);
+  if (e != cudaSuccess) return e;
+  k_carrier_fft<N><<<s.D * s.B, Cfg<N>::T, Cfg<N>::smem, stream>>>(d_Z, s.fs, s.coh, s.B, s.dopp_min, s.dopp_step,
+                                                                   d_group, d_Y);
   return cudaGetLastError();
 }
 
-cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, float2* d_Y, cudaStream_t stream) {
-  GNSS_DISPATCH_N(s.N, return wipe_fft_n<NN>(s, d_samples, d_Y, stream));
+cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const int* d_group, const int* d_gkey,
+                            float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream) {
+  GNSS_DISPATCH_N(s.N, return wipe_fft_n<NN>(s, d_samples, d_group, d_gkey, d_Z, d_Y, d_counters, stream));
 }
 
 template <int N>
-static cudaError_t xcorr_n(const AcqShape& s, const float2* d_Y, const float2* d_cspec, float* d_surface,
-                           RowStat* d_rows, cudaStream_t stream) {
+static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t stream) {
   const int grid = s.P * s.D;
   if (s.sets == 2) {
     cudaError_t e = set_smem(k_xcorr<N, true>, Cfg<N>::smem);
     if (e != cudaSuccess) return e;
-    k_xcorr<N, true><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(d_Y, d_cspec, s.B, s.D, s.P, s.excl, d_surface,
-                                                              d_rows);
+    k_xcorr<N, true><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a);
   } else {
     cudaError_t e = set_smem(k_xcorr<N, false>, Cfg<N>::smem);
     if (e != cudaSuccess) return e;
-    k_xcorr<N, false><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(d_Y, d_cspec, s.B, s.D, s.P, s.excl, d_surface,
-                                                               d_rows);
+    k_xcorr<N, false><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_cspec, float* d_surface,
-                         RowStat* d_rows, cudaStream_t stream) {
-  GNSS_DISPATCH_N(s.N, return xcorr_n<NN>(s, d_Y, d_cspec, d_surface, d_rows, stream));
+cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_cspec, const int* d_prns,
+                         float* d_surface, RowStat* d_rows, unsigned* d_counters, gnss_detection* d_out,
+                         cudaStream_t stream) {
+  XcorrArgs a;
+  a.Y = d_Y;
+  a.cspec = d_cspec;
+  a.B = s.B;
+  a.D = s.D;
+  a.P = s.P;
+  a.excl = s.excl;
+  a.surface = d_surface;
+  a.rows = d_rows;
+  a.counters = d_counters;
+  a.prns = d_prns;
+  a.out = d_out;
+  a.dopp_min = s.dopp_min;
+  a.dopp_step = s.dopp_step;
+  a.threshold = s.threshold;
+  a.second_whole = s.second_whole;
+  GNSS_DISPATCH_N(s.N, return xcorr_n<NN>(s, a, stream));
 }
 
-cudaError_t launch_peak(const AcqShape& s, const RowStat* d_rows, const int* d_prns, const float* d_surface,
-                        gnss_detection* d_out, cudaStream_t stream) {
-  k_peak<<<s.P, 32, 0, stream>>>(d_rows, d_prns, d_surface, s.P, s.D, s.N, s.sets, s.excl, s.dopp_min,
-                                 s.dopp_step, s.threshold, s.second_whole, d_out);
-  return cudaGetLastError();
+AcqScratch scratch_layout(const AcqShape& s) {
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  AcqScratch L;
+  L.z = 0;
+  L.y = L.z + al((size_t)s.G * s.B * s.N * sizeof(float2));
+  L.rows = L.y + al((size_t)s.D * s.B * s.N * sizeof(float2));
+  L.counters = L.rows + al((size_t)s.sets * s.P * s.D * sizeof(RowStat));
+  L.total = L.counters + al((size_t)s.P * sizeof(unsigned));
+  return L;
 }
 
 }  // namespace gnss

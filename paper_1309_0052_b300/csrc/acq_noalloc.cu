@@ -52,8 +52,6 @@ gnss_status scratch_address(int dev, void** out) {
   return GNSS_OK;
 }
 
-size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 }  // namespace
 
 extern "C" GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void* samples_dev, size_t n_samples,
@@ -88,24 +86,13 @@ extern "C" GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void
     set_error("gnss_acquire_noalloc: GNSS_SECOND_WHOLE needs a surface buffer");
     return GNSS_EINVAL;
   }
-  const size_t y_bytes = round256((size_t)plan->D * B * plan->N * sizeof(float2));
-  const size_t row_bytes = round256((size_t)plan->sets * plan->P * plan->D * sizeof(RowStat));
-  if (y_bytes + row_bytes > GNSS_NOALLOC_SCRATCH_BYTES) {
-    set_error("gnss_acquire_noalloc: this request needs " + std::to_string(y_bytes + row_bytes) +
-              " bytes of scratch (n_dopp * blocks * N * 8 + rows), more than the fixed " +
-              std::to_string((size_t)GNSS_NOALLOC_SCRATCH_BYTES) + " bytes");
-    return GNSS_EINVAL;
-  }
-  void* base = nullptr;
-  gnss_status st = scratch_address(dev, &base);
-  if (st != GNSS_OK) return st;
-
   AcqShape s;
   s.fs = (int)plan->desc.fs_hz;
   s.N = plan->N;
   s.coh = (int)plan->desc.coh_ms;
   s.B = (int)B;
   s.D = plan->D;
+  s.G = plan->G;
   s.P = plan->P;
   s.sets = plan->sets;
   s.excl = plan->excl;
@@ -114,15 +101,29 @@ extern "C" GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void
   s.format = (int)plan->desc.format;
   s.second_whole = (plan->desc.flags & GNSS_SECOND_WHOLE) ? 1 : 0;
   s.threshold = plan->desc.threshold;
-  // Every cell of the spectra and every row statistic that the later kernels
-  // read is written first by this call, so the previous call's contents need
-  // no clearing.
-  float2* d_Y = reinterpret_cast<float2*>(base);
-  RowStat* d_rows = reinterpret_cast<RowStat*>(reinterpret_cast<unsigned char*>(base) + y_bytes);
+  const AcqScratch lay = scratch_layout(s);
+  if (lay.total > GNSS_NOALLOC_SCRATCH_BYTES) {
+    set_error("gnss_acquire_noalloc: this request needs " + std::to_string(lay.total) +
+              " bytes of scratch (folded blocks, n_dopp * blocks * N * 8 bytes of spectra, row statistics),"
+              " more than the fixed " + std::to_string((size_t)GNSS_NOALLOC_SCRATCH_BYTES) + " bytes");
+    return GNSS_EINVAL;
+  }
+  void* base = nullptr;
+  gnss_status st = scratch_address(dev, &base);
+  if (st != GNSS_OK) return st;
+
+  // Every value the kernels read is written earlier in this call (the
+  // per-PRN counters are cleared by the first kernel), so the previous
+  // call's contents need no clearing.
+  unsigned char* sb = reinterpret_cast<unsigned char*>(base);
   cudaStream_t cs = (cudaStream_t)stream;
-  e = launch_wipe_fft(s, (const uint8_t*)samples_dev, d_Y, cs);
-  if (e == cudaSuccess) e = launch_xcorr(s, d_Y, plan->d_cspec, surface_dev, d_rows, cs);
-  if (e == cudaSuccess) e = launch_peak(s, d_rows, plan->d_prns, surface_dev, out_dev, cs);
+  e = launch_wipe_fft(s, (const uint8_t*)samples_dev, plan->d_group, plan->d_gkey,
+                      reinterpret_cast<float2*>(sb + lay.z), reinterpret_cast<float2*>(sb + lay.y),
+                      reinterpret_cast<unsigned*>(sb + lay.counters), cs);
+  if (e == cudaSuccess)
+    e = launch_xcorr(s, reinterpret_cast<const float2*>(sb + lay.y), plan->d_cspec, plan->d_prns, surface_dev,
+                     reinterpret_cast<RowStat*>(sb + lay.rows), reinterpret_cast<unsigned*>(sb + lay.counters),
+                     out_dev, cs);
   if (e != cudaSuccess) {
     set_error(std::string("gnss_acquire_noalloc: ") + cudaGetErrorString(e));
     return GNSS_ECUDA;

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -83,6 +84,7 @@ static AcqShape shape_of(const gnss_plan* plan, int B) {
   s.coh = (int)plan->desc.coh_ms;
   s.B = B;
   s.D = plan->D;
+  s.G = plan->G;
   s.P = plan->P;
   s.sets = plan->sets;
   s.excl = plan->excl;
@@ -119,27 +121,28 @@ static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_s
   if ((plan->desc.flags & GNSS_SECOND_WHOLE) && !surface_dev)
     return fail(GNSS_EINVAL, "GNSS_SECOND_WHOLE needs a surface buffer");
   const AcqShape s = shape_of(plan, B);
-  const size_t y_bytes = align256((size_t)s.D * s.B * s.N * sizeof(float2));
-  const size_t row_bytes = align256((size_t)s.sets * s.P * s.D * sizeof(RowStat));
-  const size_t det_bytes = align256((size_t)s.P * sizeof(gnss_detection));
+  const AcqScratch lay = scratch_layout(s);
   const size_t smp_bytes = samples_on_device ? 0 : align256(rec_bytes(plan->desc.format, (size_t)B * s.coh * s.N));
+  const size_t det_bytes = out_dev ? 0 : align256((size_t)s.P * sizeof(gnss_detection));
   char* ws = nullptr;
-  st = scratch_alloc(plan->device, y_bytes + row_bytes + det_bytes + smp_bytes, stream, (void**)&ws);
+  st = scratch_alloc(plan->device, lay.total + det_bytes + smp_bytes, stream, (void**)&ws);
   if (st != GNSS_OK) return st;
-  float2* d_Y = reinterpret_cast<float2*>(ws);
-  RowStat* d_rows = reinterpret_cast<RowStat*>(ws + y_bytes);
-  gnss_detection* d_det = out_dev ? out_dev : reinterpret_cast<gnss_detection*>(ws + y_bytes + row_bytes);
+  float2* d_Z = reinterpret_cast<float2*>(ws + lay.z);
+  float2* d_Y = reinterpret_cast<float2*>(ws + lay.y);
+  RowStat* d_rows = reinterpret_cast<RowStat*>(ws + lay.rows);
+  unsigned* d_cnt = reinterpret_cast<unsigned*>(ws + lay.counters);
+  gnss_detection* d_det = out_dev ? out_dev : reinterpret_cast<gnss_detection*>(ws + lay.total);
   const uint8_t* d_smp = reinterpret_cast<const uint8_t*>(samples);
   cudaError_t e = cudaSuccess;
   if (!samples_on_device) {
-    uint8_t* dst = reinterpret_cast<uint8_t*>(ws + y_bytes + row_bytes + det_bytes);
+    uint8_t* dst = reinterpret_cast<uint8_t*>(ws + lay.total + det_bytes);
     e = cudaMemcpyAsync(dst, samples, rec_bytes(plan->desc.format, (size_t)B * s.coh * s.N),
                         cudaMemcpyHostToDevice, stream);
     d_smp = dst;
   }
-  if (e == cudaSuccess) e = launch_wipe_fft(s, d_smp, d_Y, stream);
-  if (e == cudaSuccess) e = launch_xcorr(s, d_Y, plan->d_cspec, surface_dev, d_rows, stream);
-  if (e == cudaSuccess) e = launch_peak(s, d_rows, plan->d_prns, surface_dev, d_det, stream);
+  if (e == cudaSuccess) e = launch_wipe_fft(s, d_smp, plan->d_group, plan->d_gkey, d_Z, d_Y, d_cnt, stream);
+  if (e == cudaSuccess)
+    e = launch_xcorr(s, d_Y, plan->d_cspec, plan->d_prns, surface_dev, d_rows, d_cnt, d_det, stream);
   if (e == cudaSuccess && out_host)
     e = cudaMemcpyAsync(out_host, d_det, (size_t)s.P * sizeof(gnss_detection), cudaMemcpyDeviceToHost, stream);
   cudaError_t ef = cudaFreeAsync(ws, stream);
@@ -189,13 +192,33 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   p->excl = (N + 1022) / 1023;
   for (int prn = 1; prn <= 32; ++prn)
     if (d.prn_mask >> (prn - 1) & 1ull) p->prns[p->P++] = prn;
+  // Fold groups: the per-millisecond wipe-off factor exp(-j 2 pi (f i mod 1000) / 1000)
+  // depends on f only through f mod 1000 (and not at all with one coherent ms).
+  std::vector<int> group(p->D), gkey;
+  for (int k = 0; k < p->D; ++k) {
+    const int64_t f = (int64_t)d.dopp_min_hz + (int64_t)k * d.dopp_step_hz;
+    const int key = d.coh_ms == 1 ? 0 : (int)(((f % 1000) + 1000) % 1000);
+    int gi = -1;
+    for (size_t q = 0; q < gkey.size(); ++q)
+      if (gkey[q] == key) gi = (int)q;
+    if (gi < 0) {
+      gi = (int)gkey.size();
+      gkey.push_back(key);
+    }
+    group[k] = gi;
+  }
+  p->G = (int)gkey.size();
   cudaError_t e = cudaGetDevice(&p->device);
   cudaStream_t st = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_prns, sizeof(int) * p->P);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_codes, (size_t)p->P * 1023);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_cspec, (size_t)p->P * N * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_group, sizeof(int) * p->D);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_gkey, sizeof(int) * p->G);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_prns, p->prns, sizeof(int) * p->P, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_group, group.data(), sizeof(int) * p->D, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_gkey, gkey.data(), sizeof(int) * p->G, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_gold(p->d_prns, p->P, p->d_codes, st);
   if (e == cudaSuccess) e = launch_code_spectra(p->d_codes, p->P, N, p->d_cspec, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -206,6 +229,8 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
     cudaFree(p->d_prns);
     cudaFree(p->d_codes);
     cudaFree(p->d_cspec);
+    cudaFree(p->d_group);
+    cudaFree(p->d_gkey);
     delete p;
     return r;
   }
@@ -218,6 +243,8 @@ gnss_status gnss_plan_destroy(gnss_plan* plan) {
   cudaFree(plan->d_prns);
   cudaFree(plan->d_codes);
   cudaFree(plan->d_cspec);
+  cudaFree(plan->d_group);
+  cudaFree(plan->d_gkey);
   delete plan;
   return GNSS_OK;
 }
@@ -270,8 +297,16 @@ gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_dev, size_t
   const size_t L = (size_t)plan->desc.coh_ms * plan->N;
   if (n_blocks < 1 || (size_t)n_blocks > n_samples / L) return fail(GNSS_EINVAL, "n_blocks out of range");
   const AcqShape s = shape_of(plan, (int)n_blocks);
-  cudaError_t e = launch_wipe_fft(s, (const uint8_t*)samples_dev, (float2*)spectra_dev, (cudaStream_t)stream);
+  const AcqScratch lay = scratch_layout(s);
+  cudaStream_t cs = (cudaStream_t)stream;
+  float2* d_Z = nullptr;
+  st = scratch_alloc(plan->device, lay.y - lay.z, cs, (void**)&d_Z);
+  if (st != GNSS_OK) return st;
+  cudaError_t e = launch_wipe_fft(s, (const uint8_t*)samples_dev, plan->d_group, plan->d_gkey, d_Z,
+                                  (float2*)spectra_dev, nullptr, cs);
+  cudaError_t ef = cudaFreeAsync(d_Z, cs);
   if (e != cudaSuccess) return cuda_fail(e, "gnss_stage_wipe_fft");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
   return GNSS_OK;
 }
 
@@ -283,13 +318,17 @@ gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint
   if ((plan->desc.flags & GNSS_SECOND_WHOLE) && !surface_dev)
     return fail(GNSS_EINVAL, "GNSS_SECOND_WHOLE needs a surface buffer");
   const AcqShape s = shape_of(plan, (int)n_blocks);
+  const AcqScratch lay = scratch_layout(s);
   cudaStream_t cs = (cudaStream_t)stream;
-  RowStat* rows = nullptr;
-  st = scratch_alloc(plan->device, (size_t)s.sets * s.P * s.D * sizeof(RowStat), cs, (void**)&rows);
+  char* ws = nullptr;
+  st = scratch_alloc(plan->device, lay.total - lay.rows, cs, (void**)&ws);
   if (st != GNSS_OK) return st;
-  cudaError_t e = launch_xcorr(s, (const float2*)spectra_dev, plan->d_cspec, surface_dev, rows, cs);
-  if (e == cudaSuccess) e = launch_peak(s, rows, plan->d_prns, surface_dev, out_dev, cs);
-  cudaError_t ef = cudaFreeAsync(rows, cs);
+  RowStat* rows = reinterpret_cast<RowStat*>(ws);
+  unsigned* cnt = reinterpret_cast<unsigned*>(ws + (lay.counters - lay.rows));
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * s.P, cs);
+  if (e == cudaSuccess)
+    e = launch_xcorr(s, (const float2*)spectra_dev, plan->d_cspec, plan->d_prns, surface_dev, rows, cnt, out_dev, cs);
+  cudaError_t ef = cudaFreeAsync(ws, cs);
   if (e != cudaSuccess) return cuda_fail(e, "gnss_stage_correlate");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
   return GNSS_OK;

@@ -27,6 +27,7 @@ struct AcqShape {
   int coh;         // coherent ms per block
   int B;           // blocks processed
   int D;           // Doppler bins
+  int G;           // fold groups (bins sharing f mod 1000; 1 when coh == 1)
   int P;           // PRNs
   int sets;        // 1, or 2 with half-bit sets
   int excl;        // second-peak exclusion half-width (samples)
@@ -37,14 +38,43 @@ struct AcqShape {
   float threshold;
 };
 
+// Kernel arguments of the correlate + detection kernel.
+struct XcorrArgs {
+  const float2* Y;        // [D][B][N] spectra of the wiped, folded blocks
+  const float2* cspec;    // [P][N] code spectra
+  int B, D, P, excl;
+  float* surface;         // NULL or [sets][P][D][N]
+  RowStat* rows;          // [sets][P][D]
+  unsigned* counters;     // [P] zero on entry: CTAs finished per PRN
+  const int* prns;        // [P]
+  gnss_detection* out;    // [P]
+  int dopp_min, dopp_step;
+  float threshold;
+  int second_whole;
+};
+
+// Byte offsets of one acquisition's scratch (each piece 256-byte aligned).
+struct AcqScratch {
+  size_t z;         // float2 [G][B][N]  folded blocks
+  size_t y;         // float2 [D][B][N]  spectra
+  size_t rows;      // RowStat [sets][P][D]
+  size_t counters;  // unsigned [P]
+  size_t total;
+};
+AcqScratch scratch_layout(const AcqShape& s);
+
 // Launchers (acq.cu).  All are asynchronous on 'stream'.
 cudaError_t launch_gold(const int* d_prns, int P, int8_t* d_codes, cudaStream_t stream);
 cudaError_t launch_code_spectra(const int8_t* d_codes, int P, int N, float2* d_cspec, cudaStream_t stream);
-cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, float2* d_Y, cudaStream_t stream);
-cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_cspec, float* d_surface,
-                         RowStat* d_rows, cudaStream_t stream);
-cudaError_t launch_peak(const AcqShape& s, const RowStat* d_rows, const int* d_prns, const float* d_surface,
-                        gnss_detection* d_out, cudaStream_t stream);
+// k_fold + k_carrier_fft: Y from the recording.  d_counters (may be NULL) is
+// cleared for the k_xcorr launch that follows on the same stream.
+cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const int* d_group, const int* d_gkey,
+                            float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream);
+// k_xcorr: surfaces, row statistics and per-PRN detections.  d_counters must
+// be zero on entry.
+cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_cspec, const int* d_prns,
+                         float* d_surface, RowStat* d_rows, unsigned* d_counters, gnss_detection* d_out,
+                         cudaStream_t stream);
 bool supported_fft_size(int N);
 
 // Last-error message (thread-local), set by the C-ABI layer.
@@ -61,7 +91,10 @@ struct gnss_plan {
   int sets;
   int excl;
   int prns[32];
+  int G;              // fold groups
   int* d_prns;        // [P]
+  int* d_group;       // [D] fold group of each Doppler bin
+  int* d_gkey;        // [G] f mod 1000 of each group (0 when coh_ms == 1)
   int8_t* d_codes;    // [P][1023] +-1 chips
   float2* d_cspec;    // [P][N] FFT of the sampled replica
 };
