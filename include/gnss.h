@@ -229,6 +229,83 @@ GNSS_API gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_de
 GNSS_API gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint32_t n_blocks,
                                  float* surface_dev, gnss_detection* out_dev, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Fine acquisition.  The paper hands the coarse Doppler and code phase of an
+ * acquisition channel to tracking for fine tuning (Section 3, Fig. 1); here
+ * the fine tuning is gradient ascent on the coherent power of a window of
+ * L = coh_ms * N samples from the start of the recording:
+ *   z(f, tau) = sum_{n<L} x[n] exp(-j 2 pi f n / fs) ctilde(n * 1023 / N - tau - 1/2)
+ *   ctilde(u) = (1 - a) c[k mod 1023] + a c[(k+1) mod 1023],  k = floor(u), a = u - k
+ *   P(f, tau) = |z|^2     (f in Hz, tau in chips; chip k's value sits at its
+ *                          centre, so nodes are interpolated between centres)
+ * with the analytic gradient
+ *   dP/df   = 2 Re(conj(z) sum x e^{-j theta_n} (-j 2 pi n / fs) ctilde)
+ *   dP/dtau = 2 Re(conj(z) sum x e^{-j theta_n} (-(c[k+1] - c[k])))
+ * (the slope of the replica segment each sample lies on).  Sums in FP32.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint8_t prn;         /* PRN 1..32, must be in the plan's PRN set */
+  uint8_t reserved[7];
+  double f_hz;         /* start Doppler (Hz)                     */
+  double tau_chips;    /* start code delay (chips)               */
+} gnss_candidate;
+
+typedef struct {
+  double f_hz;         /* refined Doppler                         */
+  double tau_chips;    /* refined code delay                      */
+  float power;         /* P at the refined point                  */
+  uint32_t iters;      /* accepted steps                          */
+  int32_t status;      /* 0 converged (Newton step < 1e-3 Hz, tau step < 1e-5 chip), 1 stuck, 2 max_iter */
+  uint32_t reserved;
+} gnss_refined;
+
+/* P and its gradient for n (PRN, f, tau) points, one CTA per point.
+ *  samples_dev  device recording in the plan's format (16-byte aligned),
+ *               n_samples >= coh_ms * N
+ *  prn_dev      int32 [n]; f_dev, tau_dev double [n] (device)
+ *  P_dev        float [n] (device); dPdf_dev, dPdtau_dev float [n] or NULL
+ * Asynchronous on 'stream'.  Errors: GNSS_EINVAL, GNSS_ECUDA. */
+GNSS_API gnss_status gnss_refine_eval(gnss_plan* plan, const void* samples_dev, size_t n_samples, uint32_t coh_ms,
+                                      const int32_t* prn_dev, const double* f_dev, const double* tau_dev, size_t n,
+                                      float* P_dev, float* dPdf_dev, float* dPdtau_dev, void* stream);
+
+/* Gradient ascent from each candidate, entirely on the device (one CTA per
+ * candidate).
+ *  Doppler pre-search: with search_hz > 0, P is first evaluated at
+ *   f0 + k d, d = fs / (2 L) (half the main-lobe width), k = -1, +1, ...,
+ *   +-floor(search_hz / d), and the ascent starts from the first largest
+ *   value (f0 itself first).  A coarse Doppler bin wider than the coherent
+ *   window's main lobe (1 / T) needs search_hz of about half the bin.
+ *  Each iteration then moves f, then tau:
+ *   f:   Newton step g_f / (P (2 pi)^2 T^2 / 6) (closed-form peak curvature,
+ *        T = L / fs); trials alpha = 1, 1/2, ... (up to 20 halvings), taking
+ *        the first that satisfies Armijo (c1 = 1e-4) or that reduces |dP/df|
+ *        while losing at most 1e-5 of P (near the peak a change of P is below
+ *        single-precision resolution but the gradient still resolves it);
+ *   tau: sign step s_tau sign(g_tau), s_tau starting at 0.05 chip and
+ *        shrinking by the accepted backtracking factor, with Armijo; when
+ *        every trial fails, the opposite direction is tried (the segment
+ *        slope is one-sided where samples sit exactly on a kink); when both
+ *        fail, tau sits on the kink of the peak and s_tau shrinks by 2^20.
+ *  Converged (status 0) when the Newton step in f is below 1e-3 Hz and s_tau
+ *  below 1e-5 chip; stuck (status 1) when neither coordinate moves; status 2
+ *  after max_iter iterations.
+ *  samples            host recording, or device (16-byte aligned) when samples_on_device
+ *  cands, out         host arrays of n_cand records
+ * 'out' is valid once the stream has synchronised (a NULL stream is
+ * synchronised before the call returns).  Errors: GNSS_EINVAL (window longer
+ * than the recording, search_hz outside [0, 1e6], NULL), GNSS_ENOMEM,
+ * GNSS_ECUDA. */
+GNSS_API gnss_status gnss_refine(gnss_plan* plan, const void* samples, size_t n_samples, int samples_on_device,
+                                 const gnss_candidate* cands, size_t n_cand, uint32_t coh_ms, uint32_t max_iter,
+                                 double search_hz, gnss_refined* out, void* stream);
+
+/* Device-resident form of gnss_refine: samples_dev, cands_dev and out_dev
+ * are device pointers; never synchronises. */
+GNSS_API gnss_status gnss_refine_device(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                        const gnss_candidate* cands_dev, size_t n_cand, uint32_t coh_ms,
+                                        uint32_t max_iter, double search_hz, gnss_refined* out_dev, void* stream);
+
 /* FP32 FMA throughput probe (a measurement aid with no counterpart in the
  * paper; it states the ALU roof the acquisition kernels are held against):
  * 'iters' rounds of 128 dependent-chain FMAs per thread, 4 CTAs of 512

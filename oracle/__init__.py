@@ -64,7 +64,7 @@ def _L():
         _lib.orc_surfaces.argtypes = [P, P, i64, i64, i, i, i, P, i, P, i, i, P]
         _lib.orc_detect.argtypes = [P, i, i, i, i, i, i, d, P, P]
         _lib.orc_refine_eval.argtypes = [P, P, i64, d, P, d, d, P, P]
-        _lib.orc_refine.argtypes = [P, P, i64, d, P, d, d, i, P]
+        _lib.orc_refine.argtypes = [P, P, i64, d, P, d, d, i, d, P]
     return _lib
 
 
@@ -233,11 +233,13 @@ def refine_eval(x, L: int, fs: float, chips, f: float, tau: float):
     return P.value, g
 
 
-def refine(x, L: int, fs: float, chips, f0: float, tau0: float, max_iter: int = 100) -> dict:
-    """Gradient-ascent fine acquisition from (f0 Hz, tau0 chips)."""
+def refine(x, L: int, fs: float, chips, f0: float, tau0: float, max_iter: int = 100,
+           search_hz: float = 0.0) -> dict:
+    """Gradient-ascent fine acquisition from (f0 Hz, tau0 chips), after a
+    Doppler pre-search over +-search_hz at half-lobe spacing fs / (2 L)."""
     xr, xi = _split(x)
     chips = np.ascontiguousarray(chips, np.float64)
     r = _Refined()
     _L().orc_refine(_p(xr), _p(xi), int(L), float(fs), _p(chips), float(f0), float(tau0),
-                    int(max_iter), C.byref(r))
+                    int(max_iter), float(search_hz), C.byref(r))
     return dict(f=r.f, tau=r.tau, P=r.P, iters=r.iters, status=r.status)

@@ -520,53 +520,123 @@ typedef struct {
 } orc_refined;
 
 /* Gradient ascent on P(f, tau) (coarse-to-fine hand-off of Section 3, Fig. 1;
- * the step rule is this library's reading, the paper gives none):
- *   d_f   = g_f / (P (2 pi)^2 T^2 / 6)   (Newton step with the closed-form
- *                                         peak curvature, T = L / fs)
- *   d_tau = s_tau sign(g_tau)            (s_tau starts at step0 chip)
- * Armijo backtracking: alpha = 1, 1/2, ... (at most max_halvings halvings)
- * until P(f + alpha d_f, tau + alpha d_tau) >= P + c1 alpha (g_f d_f +
- * g_tau d_tau).  After an accepted step s_tau <- alpha s_tau.  Stop when no
- * alpha is accepted, when |alpha d_tau| < tol_tau and |alpha d_f| < tol_f,
- * or after max_iter iterations. */
+ * the step rule is this library's reading, the paper gives none).
+ * Doppler pre-search: with search_hz > 0, P(f0 + k d, tau0) is evaluated for
+ * d = fs / (2 L) (half the main-lobe width 1/T) and k = +-1 .. +-K,
+ * K = floor(search_hz / d), in the order -1, +1, -2, +2, ..., and the ascent
+ * starts from the first largest value (f0 itself first).  Then each
+ * iteration moves the two coordinates in turn:
+ *   f:   Newton step d_f = g_f / (P (2 pi)^2 T^2 / 6) (closed-form peak
+ *        curvature, T = L / fs); trials alpha = 1, 1/2, ... (at most
+ *        max_halvings halvings); the first trial is taken when Armijo holds,
+ *        P(new) >= P + c1 alpha g_f d_f, or when it reduces |dP/df| without
+ *        losing more than 1e-5 of P (near the peak, where the change of P is
+ *        below single-precision resolution, the gradient still resolves it);
+ *   tau: sign step d_tau = s_tau sign(g_tau) (s_tau starts at step0 chip)
+ *        with Armijo backtracking, then s_tau <- alpha s_tau.  The slope of
+ *        the replica segment is one-sided where samples sit exactly on a
+ *        kink, so when every trial fails the opposite direction is tried
+ *        (taking the first trial that raises P).
+ * When every tau trial on both sides, down to s_tau / 2^max_halvings, lowers
+ * P, tau sits on the kink of the peak and s_tau is shrunk by that factor.  P and the
+ * gradient are re-evaluated after every accepted step.  Stop as converged
+ * (status 0) when the Newton step |d_f| is below tol_f Hz and s_tau below
+ * tol_tau chip, as stuck (status 1) when neither coordinate moved, or after
+ * max_iter iterations (status 2). */
 void orc_refine(const double *xr, const double *xi, int64_t L, double fs,
                 const double *chips, double f0, double tau0, int max_iter,
-                orc_refined *out) {
+                double search_hz, orc_refined *out) {
   const double c1 = 1e-4, step0 = 0.05, tol_tau = 1e-5, tol_f = 1e-3;
   const int max_halvings = 20;
   double T = (double)L / fs;
   double curv = (2.0 * ORC_PI) * (2.0 * ORC_PI) * T * T / 6.0;
   double f = f0, tau = tau0, P, g[2];
   double s_tau = step0;
+  if (search_hz > 0.0) {
+    double d = fs / (2.0 * (double)L);
+    int K = (int)floor(search_hz / d);
+    double best;
+    orc_refine_eval(xr, xi, L, fs, chips, f0, tau0, &best, NULL);
+    for (int k = 1; k <= K; ++k)
+      for (int sg = -1; sg <= 1; sg += 2) {
+        double fk = f0 + sg * k * d, Pk;
+        orc_refine_eval(xr, xi, L, fs, chips, fk, tau0, &Pk, NULL);
+        if (Pk > best) {
+          best = Pk;
+          f = fk;
+        }
+      }
+  }
   orc_refine_eval(xr, xi, L, fs, chips, f, tau, &P, g);
   int it = 0, status = 2;
   for (; it < max_iter; ++it) {
+    double move_f = 0.0, move_t = 0.0;
     double df = P > 0.0 ? g[0] / (P * curv) : 0.0;
-    double dt = g[1] > 0.0 ? s_tau : (g[1] < 0.0 ? -s_tau : 0.0);
-    double slope = g[0] * df + g[1] * dt;
-    double alpha = 1.0, Pn = 0.0;
-    int accepted = 0;
-    for (int h = 0; h <= max_halvings; ++h) {
-      orc_refine_eval(xr, xi, L, fs, chips, f + alpha * df, tau + alpha * dt,
-                      &Pn, NULL);
-      if (Pn >= P + c1 * alpha * slope) {
-        accepted = 1;
-        break;
+    if (df != 0.0) {
+      double alpha = 1.0;
+      for (int h = 0; h <= max_halvings; ++h) {
+        double Pn, gn[2];
+        orc_refine_eval(xr, xi, L, fs, chips, f + alpha * df, tau, &Pn, gn);
+        int armijo = Pn >= P + c1 * alpha * g[0] * df;
+        int flatter = fabs(gn[0]) < fabs(g[0]) && Pn >= (1.0 - 1e-5) * P;
+        if (armijo || flatter) {
+          f += alpha * df;
+          move_f = fabs(alpha * df);
+          P = Pn;
+          g[0] = gn[0];
+          g[1] = gn[1];
+          break;
+        }
+        alpha *= 0.5;
       }
-      alpha *= 0.5;
     }
-    if (!accepted) {
-      status = 1;
-      break;
+    double dt = g[1] > 0.0 ? s_tau : (g[1] < 0.0 ? -s_tau : 0.0);
+    if (dt == 0.0) {
+      s_tau = 0.0; /* exactly flat in tau */
+    } else {
+      double alpha = 1.0;
+      int accepted = 0;
+      for (int h = 0; h <= max_halvings; ++h) {
+        double Pn;
+        orc_refine_eval(xr, xi, L, fs, chips, f, tau + alpha * dt, &Pn, NULL);
+        if (Pn >= P + c1 * alpha * g[1] * dt) {
+          tau += alpha * dt;
+          s_tau *= alpha;
+          move_t = fabs(alpha * dt);
+          orc_refine_eval(xr, xi, L, fs, chips, f, tau, &P, g);
+          accepted = 1;
+          break;
+        }
+        alpha *= 0.5;
+      }
+      /* At a kink the segment slope is one-sided: try the other direction
+       * (strict increase of P), then treat tau as sitting on the kink. */
+      if (!accepted) {
+        alpha = 1.0;
+        for (int h = 0; h <= max_halvings; ++h) {
+          double Pn;
+          orc_refine_eval(xr, xi, L, fs, chips, f, tau - alpha * dt, &Pn, NULL);
+          if (Pn > P) {
+            tau -= alpha * dt;
+            s_tau *= alpha;
+            move_t = fabs(alpha * dt);
+            orc_refine_eval(xr, xi, L, fs, chips, f, tau, &P, g);
+            accepted = 1;
+            break;
+          }
+          alpha *= 0.5;
+        }
+      }
+      /* every trial down to s_tau / 2^20 on both sides lowered P */
+      if (!accepted) s_tau = ldexp(s_tau, -max_halvings);
     }
-    f += alpha * df;
-    tau += alpha * dt;
-    s_tau *= alpha;
-    int small = fabs(alpha * dt) < tol_tau && fabs(alpha * df) < tol_f;
-    orc_refine_eval(xr, xi, L, fs, chips, f, tau, &P, g);
-    if (small) {
+    if (fabs(df) < tol_f && s_tau < tol_tau) {
       status = 0;
       ++it;
+      break;
+    }
+    if (move_f == 0.0 && move_t == 0.0) {
+      status = 1;
       break;
     }
   }

@@ -37,6 +37,11 @@ class PlanInfo(C.Structure):
                 ("excl", C.c_uint32), ("block_len", C.c_uint32)]
 
 
+CANDIDATE_DTYPE = np.dtype([("prn", "u1"), ("reserved", "u1", (7,)), ("f_hz", "<f8"), ("tau_chips", "<f8")])
+REFINED_DTYPE = np.dtype([("f_hz", "<f8"), ("tau_chips", "<f8"), ("power", "<f4"), ("iters", "<u4"),
+                          ("status", "<i4"), ("reserved", "<u4")])
+assert CANDIDATE_DTYPE.itemsize == 24 and REFINED_DTYPE.itemsize == 32
+
 DETECTION_DTYPE = np.dtype([("prn", "u1"), ("detected", "u1"), ("set", "u1"), ("reserved", "u1"),
                             ("dopp_bin", "<i4"), ("dopp_hz", "<i4"), ("code_phase", "<u4"),
                             ("peak", "<f4"), ("second", "<f4"), ("ratio", "<f4")])
@@ -55,6 +60,10 @@ _SIGS = {
     "gnss_acquire_device": ([_P, _P, C.c_size_t, _P, _P, _P], _st),
     "gnss_stage_wipe_fft": ([_P, _P, C.c_size_t, C.c_uint32, _P, _P], _st),
     "gnss_stage_correlate": ([_P, _P, C.c_uint32, _P, _P, _P], _st),
+    "gnss_refine_eval": ([_P, _P, C.c_size_t, C.c_uint32, _P, _P, _P, C.c_size_t, _P, _P, _P, _P], _st),
+    "gnss_refine": ([_P, _P, C.c_size_t, C.c_int, _P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_double, _P, _P],
+                    _st),
+    "gnss_refine_device": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_double, _P, _P], _st),
     "gnss_probe_ffma": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], _st),
     "gnss_last_error": ([], C.c_char_p),
 }
@@ -206,9 +215,48 @@ class Plan:
         check(load().gnss_stage_wipe_fft(self._h, _ptr(samples_dev), n_samples, n_blocks, _ptr(spectra_dev),
                                       _stream_ptr(stream)), "gnss_stage_wipe_fft")
 
+    def refine(self, samples, n_samples: int, cands: np.ndarray, coh_ms: int, max_iter: int = 100,
+               search_hz: float = 0.0, stream=None) -> np.ndarray:
+        """gnss_refine: Doppler pre-search over +-search_hz, then gradient
+        ascent from each candidate (records from candidates()).  samples:
+        numpy (host) or CUDA tensor.  Synchronises."""
+        cands = np.ascontiguousarray(cands, CANDIDATE_DTYPE)
+        out = np.zeros(len(cands), REFINED_DTYPE)
+        on_dev = int(hasattr(samples, "is_cuda") and samples.is_cuda)
+        if not on_dev:
+            samples = np.ascontiguousarray(samples)
+        check(load().gnss_refine(self._h, _ptr(samples), n_samples, on_dev, cands.ctypes.data, len(cands), coh_ms,
+                                 max_iter, search_hz, out.ctypes.data, _stream_ptr(stream)), "gnss_refine")
+        if stream is not None:
+            stream.synchronize()
+        return out
+
+    def refine_device(self, samples_dev, n_samples: int, cands_dev, n_cand: int, coh_ms: int, max_iter: int,
+                      out_dev, search_hz: float = 0.0, stream=None) -> None:
+        check(load().gnss_refine_device(self._h, _ptr(samples_dev), n_samples, _ptr(cands_dev), n_cand, coh_ms,
+                                        max_iter, search_hz, _ptr(out_dev), _stream_ptr(stream)),
+              "gnss_refine_device")
+
+    def refine_eval(self, samples_dev, n_samples: int, coh_ms: int, prn_dev, f_dev, tau_dev, P_dev,
+                    dPdf_dev=None, dPdtau_dev=None, stream=None) -> None:
+        """gnss_refine_eval on CUDA tensors: prn int32, f/tau float64, outputs float32."""
+        check(load().gnss_refine_eval(self._h, _ptr(samples_dev), n_samples, coh_ms, _ptr(prn_dev), _ptr(f_dev),
+                                      _ptr(tau_dev), prn_dev.numel(), _ptr(P_dev), _ptr(dPdf_dev),
+                                      _ptr(dPdtau_dev), _stream_ptr(stream)), "gnss_refine_eval")
+
     def stage_correlate(self, spectra_dev, n_blocks: int, out_dev, surface=None, stream=None) -> None:
         check(load().gnss_stage_correlate(self._h, _ptr(spectra_dev), n_blocks, _ptr(surface), _ptr(out_dev),
                                        _stream_ptr(stream)), "gnss_stage_correlate")
+
+
+def candidates(prn, f_hz, tau_chips) -> np.ndarray:
+    """Pack candidate arrays into gnss_candidate records."""
+    prn = np.atleast_1d(np.asarray(prn))
+    out = np.zeros(len(prn), CANDIDATE_DTYPE)
+    out["prn"] = prn
+    out["f_hz"] = f_hz
+    out["tau_chips"] = tau_chips
+    return out
 
 
 def probe_ffma(iters: int = 4096, stream=None):

@@ -54,7 +54,7 @@ static cudaError_t device_pool(int dev, cudaMemPool_t* out) {
   return cudaSuccess;
 }
 
-static gnss_status scratch_alloc(int dev, size_t bytes, cudaStream_t stream, void** out) {
+gnss_status scratch_alloc(int dev, size_t bytes, cudaStream_t stream, void** out) {
   cudaMemPool_t pool;
   cudaError_t e = device_pool(dev, &pool);
   if (e != cudaSuccess) return cuda_fail(e, "memory pool");
@@ -69,7 +69,11 @@ static gnss_status scratch_alloc(int dev, size_t bytes, cudaStream_t stream, voi
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-static gnss_status check_device(const gnss_plan* plan) {
+gnss_status fail_status(gnss_status st, const std::string& msg) { return fail(st, msg); }
+gnss_status cuda_status(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+gnss_status check_plan_device(const gnss_plan* plan);
+
+gnss_status check_plan_device(const gnss_plan* plan) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -113,7 +117,7 @@ static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_s
                                 gnss_detection* out_host, gnss_detection* out_dev, float* surface_dev,
                                 cudaStream_t stream) {
   if (!plan || !samples || (!out_host && !out_dev)) return fail(GNSS_EINVAL, "NULL argument");
-  gnss_status st = check_device(plan);
+  gnss_status st = check_plan_device(plan);
   if (st != GNSS_OK) return st;
   const int B = blocks_of(plan, n_samples);
   if (B < 1) return fail(GNSS_EINVAL, "n_samples is shorter than one coherent block");
@@ -216,6 +220,11 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   if (e == cudaSuccess) e = cudaMalloc(&p->d_cspec, (size_t)p->P * N * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_group, sizeof(int) * p->D);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_gkey, sizeof(int) * p->G);
+  int prn_index[33];
+  for (int k = 0; k < 33; ++k) prn_index[k] = -1;
+  for (int k = 0; k < p->P; ++k) prn_index[p->prns[k]] = k;
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_prn_index, sizeof(prn_index));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_prn_index, prn_index, sizeof(prn_index), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_prns, p->prns, sizeof(int) * p->P, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_group, group.data(), sizeof(int) * p->D, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_gkey, gkey.data(), sizeof(int) * p->G, cudaMemcpyHostToDevice, st);
@@ -231,6 +240,7 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
     cudaFree(p->d_cspec);
     cudaFree(p->d_group);
     cudaFree(p->d_gkey);
+    cudaFree(p->d_prn_index);
     delete p;
     return r;
   }
@@ -245,6 +255,7 @@ gnss_status gnss_plan_destroy(gnss_plan* plan) {
   cudaFree(plan->d_cspec);
   cudaFree(plan->d_group);
   cudaFree(plan->d_gkey);
+  cudaFree(plan->d_prn_index);
   delete plan;
   return GNSS_OK;
 }
@@ -291,7 +302,7 @@ gnss_status gnss_acquire_device(gnss_plan* plan, const void* samples_dev, size_t
 gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_dev, size_t n_samples, uint32_t n_blocks,
                                 float* spectra_dev, void* stream) {
   if (!plan || !samples_dev || !spectra_dev) return fail(GNSS_EINVAL, "NULL argument");
-  gnss_status st = check_device(plan);
+  gnss_status st = check_plan_device(plan);
   if (st != GNSS_OK) return st;
   if ((uintptr_t)samples_dev & 15u) return fail(GNSS_EINVAL, "device samples must be 16-byte aligned");
   const size_t L = (size_t)plan->desc.coh_ms * plan->N;
@@ -313,7 +324,7 @@ gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_dev, size_t
 gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint32_t n_blocks, float* surface_dev,
                                  gnss_detection* out_dev, void* stream) {
   if (!plan || !spectra_dev || !out_dev || n_blocks < 1) return fail(GNSS_EINVAL, "bad argument");
-  gnss_status st = check_device(plan);
+  gnss_status st = check_plan_device(plan);
   if (st != GNSS_OK) return st;
   if ((plan->desc.flags & GNSS_SECOND_WHOLE) && !surface_dev)
     return fail(GNSS_EINVAL, "GNSS_SECOND_WHOLE needs a surface buffer");

@@ -77,6 +77,28 @@ cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_c
                          cudaStream_t stream);
 bool supported_fft_size(int N);
 
+// Fine acquisition (refine.cu).
+struct RefineJob {
+  const uint8_t* samples;  // device recording, 16-byte aligned
+  int format;
+  int N;                   // samples per ms
+  int L;                   // samples in the coherent window (from the recording start)
+  double fs;
+  const int8_t* codes;     // [P][1023] +-1
+  const int* prn_index;    // [33] plan index of PRN 1..32 (-1 = not in the plan)
+};
+cudaError_t launch_refine_eval(const RefineJob& J, int n, const int* prn, const double* f, const double* tau,
+                               float* P, float* dPdf, float* dPdtau, cudaStream_t s);
+cudaError_t launch_refine(const RefineJob& J, int n, const gnss_candidate* cands, int max_iter, double search_hz,
+                          gnss_refined* out, cudaStream_t s);
+
+// Shared C-ABI helpers (capi.cu): thread-local error message, status from a
+// CUDA error, current-device check and scratch from the library pool.
+gnss_status fail_status(gnss_status st, const std::string& msg);
+gnss_status cuda_status(cudaError_t e, const char* where);
+gnss_status check_plan_device(const gnss_plan* plan);
+gnss_status scratch_alloc(int dev, size_t bytes, cudaStream_t stream, void** out);
+
 // Last-error message (thread-local), set by the C-ABI layer.
 void set_error(const std::string& msg);
 
@@ -95,6 +117,7 @@ struct gnss_plan {
   int* d_prns;        // [P]
   int* d_group;       // [D] fold group of each Doppler bin
   int* d_gkey;        // [G] f mod 1000 of each group (0 when coh_ms == 1)
+  int* d_prn_index;   // [33] plan index of PRN 1..32, -1 when not searched
   int8_t* d_codes;    // [P][1023] +-1 chips
   float2* d_cspec;    // [P][N] FFT of the sampled replica
 };

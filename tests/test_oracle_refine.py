@@ -121,7 +121,7 @@ def test_doppler_gradient_vanishes_at_truth_noise_free():
 def test_ascent_converges_to_truth_noise_free():
     x = _signal()
     chips = oracle.ca_code(7).astype(float)
-    r = oracle.refine(x, L, FS, chips, 1234.5 + 180.0, 300.3 + 0.3)
+    r = oracle.refine(x, L, FS, chips, 1234.5 + 180.0, 300.3 + 0.3, search_hz=250.0)
     assert abs(r["f"] - 1234.5) < 1e-2
     assert abs(r["tau"] - 300.3) < 1e-3
     P0, _ = oracle.refine_eval(x, L, FS, chips, 1234.5 + 180.0, 300.3 + 0.3)
