@@ -190,6 +190,28 @@ GNSS_API gnss_status gnss_acquire(gnss_plan* plan, const void* samples, size_t n
 GNSS_API gnss_status gnss_acquire_device(gnss_plan* plan, const void* samples_dev, size_t n_samples,
                                 gnss_detection* out_dev, float* surface_dev, void* stream);
 
+/* One request of a batched acquisition. */
+typedef struct {
+  gnss_plan* plan;          /* plan of this request (fs, coherent length, Doppler grid, PRNs, format, flags) */
+  const void* samples_dev;  /* device recording in the plan's format, 16-byte aligned */
+  size_t n_samples;         /* complex samples (>= the plan's block length) */
+  gnss_detection* out_dev;  /* device, n_prn records of this plan */
+  float* surface_dev;       /* NULL or device [n_sets][n_prn][n_dopp][N] */
+} gnss_request;
+
+/* Acquire many recordings of uneven length, sample rate, Doppler grid and
+ * coherent length with one launch triple per group of requests that share
+ * FFT size, format and half-bit setting -- the batch mode of Section 5,
+ * Listing 3b, over whole requests.  Within a group the requests run longest
+ * first; groups are split into waves whose scratch (folded blocks, spectra,
+ * row statistics) stays within scratch_budget bytes (0 = 16 GiB; a request
+ * larger than the budget runs in a wave of its own).  Every request gets the
+ * same records and surfaces as gnss_acquire_device alone.  Asynchronous on
+ * 'stream'; device outputs are valid once it has synchronised.
+ * Errors: GNSS_EINVAL (any invalid request; nothing is launched),
+ * GNSS_ENOMEM, GNSS_ECUDA. */
+GNSS_API gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t scratch_budget, void* stream);
+
 /* Acquisition that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at
  * request time -- services that must keep a fixed device footprint after

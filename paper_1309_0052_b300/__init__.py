@@ -32,6 +32,11 @@ class PlanDesc(C.Structure):
                 ("format", C.c_uint32), ("reserved", C.c_uint32)]
 
 
+class Request(C.Structure):
+    _fields_ = [("plan", C.c_void_p), ("samples_dev", C.c_void_p), ("n_samples", C.c_size_t),
+                ("out_dev", C.c_void_p), ("surface_dev", C.c_void_p)]
+
+
 class PlanInfo(C.Structure):
     _fields_ = [("N", C.c_uint32), ("n_prn", C.c_uint32), ("n_dopp", C.c_uint32), ("n_sets", C.c_uint32),
                 ("excl", C.c_uint32), ("block_len", C.c_uint32)]
@@ -64,6 +69,7 @@ _SIGS = {
     "gnss_refine": ([_P, _P, C.c_size_t, C.c_int, _P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_double, _P, _P],
                     _st),
     "gnss_refine_device": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_double, _P, _P], _st),
+    "gnss_acquire_batch": ([_P, C.c_size_t, C.c_size_t, _P], _st),
     "gnss_probe_ffma": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], _st),
     "gnss_last_error": ([], C.c_char_p),
 }
@@ -247,6 +253,17 @@ class Plan:
     def stage_correlate(self, spectra_dev, n_blocks: int, out_dev, surface=None, stream=None) -> None:
         check(load().gnss_stage_correlate(self._h, _ptr(spectra_dev), n_blocks, _ptr(surface), _ptr(out_dev),
                                        _stream_ptr(stream)), "gnss_stage_correlate")
+
+
+def acquire_batch(requests, scratch_budget: int = 0, stream=None) -> None:
+    """gnss_acquire_batch.  requests: iterable of (plan, samples_dev, n_samples,
+    out_dev, surface_dev or None) with CUDA tensors.  Asynchronous."""
+    reqs = list(requests)
+    arr = (Request * len(reqs))()
+    for k, (plan, smp, n, out, surf) in enumerate(reqs):
+        arr[k] = Request(plan.handle.value if hasattr(plan.handle, "value") else plan.handle, _ptr(smp), n,
+                         _ptr(out), _ptr(surf))
+    check(load().gnss_acquire_batch(arr, len(reqs), scratch_budget, _stream_ptr(stream)), "gnss_acquire_batch")
 
 
 def candidates(prn, f_hz, tau_chips) -> np.ndarray:

@@ -161,16 +161,16 @@ struct FoldCfg {
 };
 
 template <int N, int FMT>
-__global__ void __launch_bounds__(FoldCfg<N>::T) k_fold(const uint8_t* __restrict__ samples, int coh, int B,
-                                                       const int* __restrict__ gkey, float2* __restrict__ Z,
-                                                       unsigned* __restrict__ counters, int P) {
+__device__ __forceinline__ void fold_tile(const FoldArgs& a, int tile) {
   constexpr int E = FoldCfg<N>::E, T = FoldCfg<N>::T, CPB = FoldCfg<N>::CPB;
-  const int gb = blockIdx.x / CPB;             // g * B + b
-  const int m0 = E * ((blockIdx.x % CPB) * T + threadIdx.x);
+  const uint8_t* __restrict__ samples = a.samples;
+  const int coh = a.coh, B = a.B;
+  const int gb = tile / CPB;             // g * B + b
+  const int m0 = E * ((tile % CPB) * T + threadIdx.x);
   const int g = gb / B, b = gb % B;
-  if (counters != nullptr && blockIdx.x == 0)
-    for (int p = threadIdx.x; p < P; p += T) counters[p] = 0u;
-  const int rho = gkey[g];
+  if (a.counters != nullptr && tile == 0)
+    for (int p = threadIdx.x; p < a.P; p += T) a.counters[p] = 0u;
+  const int rho = a.gkey[g];
   const int64_t n_first = (int64_t)b * coh * N + m0;  // first sample of this thread, ms 0
   float ar[E], ai[E];
 #pragma unroll
@@ -205,9 +205,31 @@ __global__ void __launch_bounds__(FoldCfg<N>::T) k_fold(const uint8_t* __restric
       ai[e] = fmaf(-3.f, wsum_r + wsum_i, ai[e]);
     }
   }
-  float4* out = reinterpret_cast<float4*>(Z + ((size_t)gb * N + m0));
+  float4* out = reinterpret_cast<float4*>(a.Z + ((size_t)gb * N + m0));
 #pragma unroll
   for (int e = 0; e < E; e += 2) out[e / 2] = make_float4(ar[e], ai[e], ar[e + 1], ai[e + 1]);
+}
+
+// Request of a batched launch that owns CTA blockIdx.x: base[r] <= blockIdx.x
+// < base[r + 1] (base ascending, base[0] = 0).  One probe per thread.
+__device__ __forceinline__ int find_request(const uint32_t* __restrict__ base, int n) {
+  __shared__ int s_req;
+  for (int r = threadIdx.x; r < n; r += blockDim.x)
+    if (__ldg(base + r) <= blockIdx.x && blockIdx.x < __ldg(base + r + 1)) s_req = r;
+  __syncthreads();
+  return s_req;
+}
+
+template <int N, int FMT>
+__global__ void __launch_bounds__(FoldCfg<N>::T) k_fold(const FoldArgs a) {
+  fold_tile<N, FMT>(a, blockIdx.x);
+}
+
+template <int N, int FMT>
+__global__ void __launch_bounds__(FoldCfg<N>::T) k_fold_batch(const BatchReq* __restrict__ reqs,
+                                                             const uint32_t* __restrict__ base, int n) {
+  const int r = find_request(base, n);
+  fold_tile<N, FMT>(reqs[r].fold, (int)(blockIdx.x - __ldg(base + r)));
 }
 
 // k_carrier_fft: one CTA per (Doppler d, block b), tile = d * B + b.  Loads the
@@ -216,17 +238,15 @@ __global__ void __launch_bounds__(FoldCfg<N>::T) k_fold(const uint8_t* __restric
 // integer phase for r = 0, then a rotation by T samples per r -- and runs
 // the forward FFT: Y_{f,b} = FFT_N(y_{f,b}).
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::T) k_carrier_fft(const float2* __restrict__ Z, int fs, int coh, int B,
-                                                          int dopp_min, int dopp_step,
-                                                          const int* __restrict__ group, float2* __restrict__ Y) {
+__device__ __forceinline__ void carrier_tile(const CarrierArgs& a, int tile, float2* sm) {
   constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
-  extern __shared__ float2 sm[];
   float2* buf0 = sm;
   float2* buf1 = Cfg<N>::DB ? sm + FftShape<N>::smem_elems : sm;
+  const int fs = a.fs, coh = a.coh, B = a.B;
   const int j = threadIdx.x;
-  const int d = blockIdx.x / B, b = blockIdx.x % B;
-  const int f = dopp_min + d * dopp_step;
-  const float2* z = Z + ((size_t)group[d] * B + b) * N;
+  const int d = tile / B, b = tile % B;
+  const int f = a.dopp_min + d * a.dopp_step;
+  const float2* z = a.Z + ((size_t)a.group[d] * B + b) * N;
   const int64_t fr = (((int64_t)f % fs) + fs) % fs;
   const int64_t r0 = (fr * ((int64_t)b * coh * N + j)) % fs;
   const int64_t rs = (fr * T) % fs;
@@ -244,9 +264,23 @@ __global__ void __launch_bounds__(Cfg<N>::T) k_carrier_fft(const float2* __restr
   }
   int phase = 0;
   fft_block<N, E, false, Cfg<N>::DB>(v, j, buf0, buf1, phase);
-  float2* out = Y + (size_t)blockIdx.x * N;
+  float2* out = a.Y + (size_t)tile * N;
 #pragma unroll
   for (int r = 0; r < E; ++r) out[j + T * r] = v[r];
+}
+
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::T) k_carrier_fft(const CarrierArgs a) {
+  extern __shared__ float2 sm[];
+  carrier_tile<N>(a, blockIdx.x, sm);
+}
+
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::T) k_carrier_fft_batch(const BatchReq* __restrict__ reqs,
+                                                                const uint32_t* __restrict__ base, int n) {
+  extern __shared__ float2 sm[];
+  const int r = find_request(base, n);
+  carrier_tile<N>(reqs[r].car, (int)(blockIdx.x - __ldg(base + r)), sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -428,17 +462,16 @@ __device__ __forceinline__ void finalize_prn(const XcorrArgs& a, int p, int sets
 }
 
 template <int N, bool HALF>
-__global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB) k_xcorr(const XcorrArgs a) {
+__device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2* sm) {
   constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
   constexpr bool DB = Cfg<N>::DB, TWC = Cfg<N>::TWC;
-  extern __shared__ float2 sm[];
   float2* buf0 = sm;
   float2* buf1 = DB ? sm + FftShape<N>::smem_elems : sm;
   __shared__ float s_val[32];
   __shared__ uint32_t s_idx[32];
   __shared__ unsigned s_last;
   const int j = threadIdx.x;
-  const int p = blockIdx.x % a.P, d = blockIdx.x / a.P;
+  const int p = tile % a.P, d = tile / a.P;
   const float2* cp = a.cspec + (size_t)p * N;
   FftTw<N, E, true> tw;
   if constexpr (TWC) tw.init(j);
@@ -476,6 +509,20 @@ __global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB) k_xcorr(const XcorrAr
     __threadfence();
     finalize_prn<N, T>(a, p, sets, s_val, s_idx);
   }
+}
+
+template <int N, bool HALF>
+__global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB) k_xcorr(const XcorrArgs a) {
+  extern __shared__ float2 sm[];
+  xcorr_tile<N, HALF>(a, blockIdx.x, sm);
+}
+
+template <int N, bool HALF>
+__global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB)
+    k_xcorr_batch(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ base, int n) {
+  extern __shared__ float2 sm[];
+  const int r = find_request(base, n);
+  xcorr_tile<N, HALF>(reqs[r].xc, (int)(blockIdx.x - __ldg(base + r)), sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -523,18 +570,16 @@ template <int N>
 static cudaError_t wipe_fft_n(const AcqShape& s, const uint8_t* d_samples, const int* d_group, const int* d_gkey,
                               float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream) {
   const int fgrid = s.G * s.B * FoldCfg<N>::CPB;
+  const FoldArgs fa = fold_args(s, d_samples, d_gkey, d_Z, d_counters);
   if (s.format == GNSS_FMT_2BIT_IQ)
-    k_fold<N, GNSS_FMT_2BIT_IQ><<<fgrid, FoldCfg<N>::T, 0, stream>>>(d_samples, s.coh, s.B, d_gkey, d_Z, d_counters,
-                                                                     s.P);
+    k_fold<N, GNSS_FMT_2BIT_IQ><<<fgrid, FoldCfg<N>::T, 0, stream>>>(fa);
   else
-    k_fold<N, GNSS_FMT_I8_IQ><<<fgrid, FoldCfg<N>::T, 0, stream>>>(d_samples, s.coh, s.B, d_gkey, d_Z, d_counters,
-                                                                   s.P);
+    k_fold<N, GNSS_FMT_I8_IQ><<<fgrid, FoldCfg<N>::T, 0, stream>>>(fa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = set_smem(k_carrier_fft<N>, Cfg<N>::smem);
   if (e != cudaSuccess) return e;
-  k_carrier_fft<N><<<s.D * s.B, Cfg<N>::T, Cfg<N>::smem, stream>>>(d_Z, s.fs, s.coh, s.B, s.dopp_min, s.dopp_step,
-                                                                   d_group, d_Y);
+  k_carrier_fft<N><<<s.D * s.B, Cfg<N>::T, Cfg<N>::smem, stream>>>(carrier_args(s, d_group, d_Z, d_Y));
   return cudaGetLastError();
 }
 
@@ -558,9 +603,34 @@ static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_cspec, const int* d_prns,
-                         float* d_surface, RowStat* d_rows, unsigned* d_counters, gnss_detection* d_out,
-                         cudaStream_t stream) {
+FoldArgs fold_args(const AcqShape& s, const uint8_t* d_samples, const int* d_gkey, float2* d_Z,
+                   unsigned* d_counters) {
+  FoldArgs a;
+  a.samples = d_samples;
+  a.gkey = d_gkey;
+  a.Z = d_Z;
+  a.counters = d_counters;
+  a.coh = s.coh;
+  a.B = s.B;
+  a.P = s.P;
+  return a;
+}
+
+CarrierArgs carrier_args(const AcqShape& s, const int* d_group, const float2* d_Z, float2* d_Y) {
+  CarrierArgs a;
+  a.Z = d_Z;
+  a.group = d_group;
+  a.Y = d_Y;
+  a.fs = s.fs;
+  a.coh = s.coh;
+  a.B = s.B;
+  a.dopp_min = s.dopp_min;
+  a.dopp_step = s.dopp_step;
+  return a;
+}
+
+XcorrArgs xcorr_args(const AcqShape& s, const float2* d_Y, const float2* d_cspec, const int* d_prns,
+                     float* d_surface, RowStat* d_rows, unsigned* d_counters, gnss_detection* d_out) {
   XcorrArgs a;
   a.Y = d_Y;
   a.cspec = d_cspec;
@@ -577,7 +647,52 @@ cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_c
   a.dopp_step = s.dopp_step;
   a.threshold = s.threshold;
   a.second_whole = s.second_whole;
+  return a;
+}
+
+cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_cspec, const int* d_prns,
+                         float* d_surface, RowStat* d_rows, unsigned* d_counters, gnss_detection* d_out,
+                         cudaStream_t stream) {
+  const XcorrArgs a = xcorr_args(s, d_Y, d_cspec, d_prns, d_surface, d_rows, d_counters, d_out);
   GNSS_DISPATCH_N(s.N, return xcorr_n<NN>(s, a, stream));
+}
+
+// Batched launches: every request of the group shares N, format and sets.
+template <int N>
+static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
+  cudaError_t e;
+  if (g.format == GNSS_FMT_2BIT_IQ)
+    k_fold_batch<N, GNSS_FMT_2BIT_IQ><<<g.fold_ctas, FoldCfg<N>::T, 0, stream>>>(g.reqs, g.fold_base, g.n);
+  else
+    k_fold_batch<N, GNSS_FMT_I8_IQ><<<g.fold_ctas, FoldCfg<N>::T, 0, stream>>>(g.reqs, g.fold_base, g.n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = set_smem(k_carrier_fft_batch<N>, Cfg<N>::smem)) != cudaSuccess) return e;
+  k_carrier_fft_batch<N><<<g.car_ctas, Cfg<N>::T, Cfg<N>::smem, stream>>>(g.reqs, g.car_base, g.n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (g.sets == 2) {
+    if ((e = set_smem(k_xcorr_batch<N, true>, Cfg<N>::smem)) != cudaSuccess) return e;
+    k_xcorr_batch<N, true><<<g.xc_ctas, Cfg<N>::T, Cfg<N>::smem, stream>>>(g.reqs, g.xc_base, g.n);
+  } else {
+    if ((e = set_smem(k_xcorr_batch<N, false>, Cfg<N>::smem)) != cudaSuccess) return e;
+    k_xcorr_batch<N, false><<<g.xc_ctas, Cfg<N>::T, Cfg<N>::smem, stream>>>(g.reqs, g.xc_base, g.n);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchGroup& g, cudaStream_t stream) {
+  GNSS_DISPATCH_N(g.N, return batch_n<NN>(g, stream));
+}
+
+uint32_t fold_ctas_per_block(int N) {
+  switch (N) {
+    case 256: return FoldCfg<256>::CPB;
+    case 512: return FoldCfg<512>::CPB;
+    case 1024: return FoldCfg<1024>::CPB;
+    case 2048: return FoldCfg<2048>::CPB;
+    case 4096: return FoldCfg<4096>::CPB;
+    case 8192: return FoldCfg<8192>::CPB;
+    default: return FoldCfg<16384>::CPB;
+  }
 }
 
 AcqScratch scratch_layout(const AcqShape& s) {

@@ -5,7 +5,10 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -342,6 +345,108 @@ gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint
   cudaError_t ef = cudaFreeAsync(ws, cs);
   if (e != cudaSuccess) return cuda_fail(e, "gnss_stage_correlate");
   if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  return GNSS_OK;
+}
+
+gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t scratch_budget, void* stream) {
+  if (n_req == 0) return GNSS_OK;
+  if (!reqs) return fail(GNSS_EINVAL, "NULL argument");
+  if (n_req > (size_t)INT32_MAX) return fail(GNSS_EINVAL, "too many requests");
+  if (scratch_budget == 0) scratch_budget = (size_t)16 << 30;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  // validate everything before launching anything
+  std::vector<AcqShape> shape(n_req);
+  std::vector<AcqScratch> lay(n_req);
+  std::map<std::tuple<int, int, int>, std::vector<size_t>> groups;
+  for (size_t i = 0; i < n_req; ++i) {
+    const gnss_request& r = reqs[i];
+    const std::string at = "request " + std::to_string(i) + ": ";
+    if (!r.plan || !r.samples_dev || !r.out_dev) return fail(GNSS_EINVAL, at + "NULL plan, samples or output");
+    if (r.plan->device != dev) return fail(GNSS_EINVAL, at + "plan belongs to another device than the current one");
+    if ((uintptr_t)r.samples_dev & 15u) return fail(GNSS_EINVAL, at + "device samples must be 16-byte aligned");
+    if ((r.plan->desc.flags & GNSS_SECOND_WHOLE) && !r.surface_dev)
+      return fail(GNSS_EINVAL, at + "GNSS_SECOND_WHOLE needs a surface buffer");
+    const int B = blocks_of(r.plan, r.n_samples);
+    if (B < 1) return fail(GNSS_EINVAL, at + "n_samples is shorter than one coherent block");
+    shape[i] = shape_of(r.plan, B);
+    lay[i] = scratch_layout(shape[i]);
+    groups[std::make_tuple(shape[i].N, shape[i].format, shape[i].sets)].push_back(i);
+  }
+  for (auto& kv : groups) {
+    std::vector<size_t>& idx = kv.second;
+    // longest correlate CTAs (most blocks) first, so the tail is short ones
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return shape[a].B > shape[b].B; });
+    size_t pos = 0;
+    while (pos < idx.size()) {
+      size_t end = pos, bytes = 0;
+      while (end < idx.size() && (end == pos || bytes + lay[idx[end]].total <= scratch_budget)) bytes += lay[idx[end++]].total;
+      const int n = (int)(end - pos);
+      const size_t desc_bytes = align256(sizeof(BatchReq) * n) + align256(3 * sizeof(uint32_t) * (n + 1));
+      char* ws = nullptr;
+      gnss_status st = scratch_alloc(dev, desc_bytes + bytes, cs, (void**)&ws);
+      if (st != GNSS_OK) return st;
+      std::vector<BatchReq> hr(n);
+      std::vector<uint32_t> hb(3 * (size_t)(n + 1));
+      uint32_t* fb = hb.data();
+      uint32_t* cb = fb + (n + 1);
+      uint32_t* xb = cb + (n + 1);
+      fb[0] = cb[0] = xb[0] = 0;
+      char* cur = ws + desc_bytes;
+      const uint32_t cpb = fold_ctas_per_block(shape[idx[pos]].N);
+      bool too_many = false;
+      for (int k = 0; k < n; ++k) {
+        const size_t i = idx[pos + k];
+        const gnss_request& r = reqs[i];
+        const AcqShape& sh = shape[i];
+        const AcqScratch& L = lay[i];
+        float2* Z = reinterpret_cast<float2*>(cur + L.z);
+        float2* Y = reinterpret_cast<float2*>(cur + L.y);
+        RowStat* rows = reinterpret_cast<RowStat*>(cur + L.rows);
+        unsigned* cnt = reinterpret_cast<unsigned*>(cur + L.counters);
+        hr[k].fold = fold_args(sh, (const uint8_t*)r.samples_dev, r.plan->d_gkey, Z, cnt);
+        hr[k].car = carrier_args(sh, r.plan->d_group, Z, Y);
+        hr[k].xc = xcorr_args(sh, Y, r.plan->d_cspec, r.plan->d_prns, r.surface_dev, rows, cnt, r.out_dev);
+        const uint64_t nf = (uint64_t)fb[k] + (uint64_t)sh.G * sh.B * cpb;
+        const uint64_t nc = (uint64_t)cb[k] + (uint64_t)sh.D * sh.B;
+        const uint64_t nx = (uint64_t)xb[k] + (uint64_t)sh.P * sh.D;
+        if (nf > INT32_MAX || nc > INT32_MAX || nx > INT32_MAX) too_many = true;
+        fb[k + 1] = (uint32_t)nf;
+        cb[k + 1] = (uint32_t)nc;
+        xb[k + 1] = (uint32_t)nx;
+        cur += L.total;
+      }
+      if (too_many) {
+        cudaFreeAsync(ws, cs);
+        return fail(GNSS_EINVAL, "a wave needs more than 2^31 CTAs; lower scratch_budget");
+      }
+      BatchReq* d_reqs = reinterpret_cast<BatchReq*>(ws);
+      uint32_t* d_base = reinterpret_cast<uint32_t*>(ws + align256(sizeof(BatchReq) * n));
+      e = cudaMemcpyAsync(d_reqs, hr.data(), sizeof(BatchReq) * n, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_base, hb.data(), sizeof(uint32_t) * hb.size(), cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) {
+        BatchGroup g;
+        g.N = std::get<0>(kv.first);
+        g.format = std::get<1>(kv.first);
+        g.sets = std::get<2>(kv.first);
+        g.n = n;
+        g.reqs = d_reqs;
+        g.fold_base = d_base;
+        g.car_base = d_base + (n + 1);
+        g.xc_base = d_base + 2 * (n + 1);
+        g.fold_ctas = fb[n];
+        g.car_ctas = cb[n];
+        g.xc_ctas = xb[n];
+        e = launch_batch(g, cs);
+      }
+      cudaError_t ef = cudaFreeAsync(ws, cs);
+      if (e != cudaSuccess) return cuda_fail(e, "gnss_acquire_batch");
+      if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+      pos = end;
+    }
+  }
   return GNSS_OK;
 }
 

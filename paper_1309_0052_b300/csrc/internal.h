@@ -53,6 +53,48 @@ struct XcorrArgs {
   int second_whole;
 };
 
+// Kernel arguments of the fold kernel (k_fold): one request.
+struct FoldArgs {
+  const uint8_t* samples;  // recording
+  const int* gkey;         // [G] f mod 1000 per fold group
+  float2* Z;               // [G][B][N] folded blocks
+  unsigned* counters;      // NULL or [P] per-PRN counters to clear
+  int coh, B, P;
+};
+
+// Kernel arguments of the carrier + forward FFT kernel (k_carrier_fft).
+struct CarrierArgs {
+  const float2* Z;         // [G][B][N]
+  const int* group;        // [D] fold group per Doppler bin
+  float2* Y;               // [D][B][N]
+  int fs, coh, B, dopp_min, dopp_step;
+};
+
+// One request of a batched launch.
+struct BatchReq {
+  FoldArgs fold;
+  CarrierArgs car;
+  XcorrArgs xc;
+};
+
+// One batched launch triple: n requests sharing N, format and sets; the CTAs
+// of request r in each kernel are [base[r], base[r + 1]).
+struct BatchGroup {
+  int N, format, sets, n;
+  const BatchReq* reqs;       // device [n]
+  const uint32_t* fold_base;  // device [n + 1]
+  const uint32_t* car_base;   // device [n + 1]
+  const uint32_t* xc_base;    // device [n + 1]
+  uint32_t fold_ctas, car_ctas, xc_ctas;
+};
+
+FoldArgs fold_args(const AcqShape& s, const uint8_t* d_samples, const int* d_gkey, float2* d_Z, unsigned* d_counters);
+CarrierArgs carrier_args(const AcqShape& s, const int* d_group, const float2* d_Z, float2* d_Y);
+XcorrArgs xcorr_args(const AcqShape& s, const float2* d_Y, const float2* d_cspec, const int* d_prns,
+                     float* d_surface, RowStat* d_rows, unsigned* d_counters, gnss_detection* d_out);
+cudaError_t launch_batch(const BatchGroup& g, cudaStream_t stream);
+uint32_t fold_ctas_per_block(int N);
+
 // Byte offsets of one acquisition's scratch (each piece 256-byte aligned).
 struct AcqScratch {
   size_t z;         // float2 [G][B][N]  folded blocks
