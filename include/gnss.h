@@ -328,6 +328,78 @@ GNSS_API gnss_status gnss_refine_device(gnss_plan* plan, const void* samples_dev
                                         const gnss_candidate* cands_dev, size_t n_cand, uint32_t coh_ms,
                                         uint32_t max_iter, double search_hz, gnss_refined* out_dev, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Serving.  The paper's cloud deployment runs many receiver instances per
+ * server and rates throughput by the effective running time of concurrent
+ * instances (Section 4); for the GPU it names fewer, larger operations as the
+ * cure for per-thread GPU calls serialising (Section 5, Listing 3b).  The
+ * server keeps plans and code spectra resident, admits submitted recordings
+ * while their device memory fits the budget, and batches every admitted
+ * request into one launch (continuous batching), with several batches in
+ * flight so that new requests overlap with running ones.
+ * ------------------------------------------------------------------------ */
+typedef struct gnss_server gnss_server;
+
+typedef struct {
+  size_t device_mem_budget;   /* device bytes held by requests in flight (0 = 16 GiB) */
+  size_t host_staging_bytes;  /* pinned host bytes for queued recordings and records (0 = 1 GiB) */
+  uint32_t max_batch;         /* requests per batched launch (0 = 64) */
+  uint32_t streams;           /* streams carrying batches, two in flight each (0 = 2, at most 16) */
+  uint32_t queue_timeout_ms;  /* fail requests still queued after this long with GNSS_ETIMEOUT (0 = never) */
+  uint32_t reserved;
+} gnss_server_config;
+
+typedef struct {
+  uint64_t submitted;
+  uint64_t completed;
+  uint64_t failed;
+  uint64_t batches;               /* batched launches so far */
+  uint64_t queued;                /* requests waiting for admission now */
+  uint32_t batches_in_flight;
+  uint32_t reserved;
+  size_t device_bytes_reserved;   /* device bytes of batches in flight now */
+} gnss_server_stats;
+
+/* Start a server on the current device (cfg NULL = defaults): allocates the
+ * pinned staging arena and the streams and starts the dispatcher thread.
+ * Errors: GNSS_EINVAL, GNSS_ENOMEM, GNSS_ECUDA. */
+GNSS_API gnss_status gnss_server_create(const gnss_server_config* cfg, gnss_server** out);
+
+/* Fail still-queued requests with GNSS_ECANCELLED, wait for batches in
+ * flight, release everything (NULL is accepted). */
+GNSS_API gnss_status gnss_server_destroy(gnss_server* srv);
+
+/* Queue one recording (host memory, copied before return: the caller may
+ * free it) for acquisition with the plan 'desc' describes; *ticket names it.
+ * Thread-safe.  Errors: GNSS_EINVAL (descriptor, length, GNSS_SECOND_WHOLE),
+ * GNSS_EBUSY (host staging full, or the request alone exceeds the device
+ * budget), GNSS_ECANCELLED (server shutting down). */
+GNSS_API gnss_status gnss_submit(gnss_server* srv, const gnss_plan_desc* desc, const void* host_samples,
+                                 size_t n_samples, uint64_t* ticket);
+
+/* Result of a request: GNSS_EAGAIN while queued or running; otherwise its
+ * status (GNSS_OK with *n records copied to out, at most cap; or the error
+ * that ended it) -- and the ticket is released. */
+GNSS_API gnss_status gnss_poll(gnss_server* srv, uint64_t ticket, gnss_detection* out, size_t cap, size_t* n);
+
+/* gnss_poll that blocks up to timeout_ms; GNSS_ETIMEOUT if the request is
+ * still queued or running then (it keeps running; poll again later). */
+GNSS_API gnss_status gnss_wait(gnss_server* srv, uint64_t ticket, uint32_t timeout_ms, gnss_detection* out,
+                               size_t cap, size_t* n);
+
+/* Cancel a request: a queued one is dropped, a running one has its records
+ * discarded; its poll then returns GNSS_ECANCELLED. */
+GNSS_API gnss_status gnss_cancel(gnss_server* srv, uint64_t ticket);
+
+/* Counters of the server. */
+GNSS_API gnss_status gnss_server_get_stats(gnss_server* srv, gnss_server_stats* out);
+
+/* Testing hook: make the k-th next device allocation of the dispatcher fail
+ * (k = 0: the next one; negative: never), as if the device were out of
+ * memory; the requests of that batch end with GNSS_ENOMEM and the server
+ * carries on.  Nothing is faulted on the device. */
+GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
+
 /* FP32 FMA throughput probe (a measurement aid with no counterpart in the
  * paper; it states the ALU roof the acquisition kernels are held against):
  * 'iters' rounds of 128 dependent-chain FMAs per thread, 4 CTAs of 512

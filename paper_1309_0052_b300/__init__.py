@@ -37,6 +37,17 @@ class Request(C.Structure):
                 ("out_dev", C.c_void_p), ("surface_dev", C.c_void_p)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("device_mem_budget", C.c_size_t), ("host_staging_bytes", C.c_size_t), ("max_batch", C.c_uint32),
+                ("streams", C.c_uint32), ("queue_timeout_ms", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("batches", C.c_uint64), ("queued", C.c_uint64), ("batches_in_flight", C.c_uint32),
+                ("reserved", C.c_uint32), ("device_bytes_reserved", C.c_size_t)]
+
+
 class PlanInfo(C.Structure):
     _fields_ = [("N", C.c_uint32), ("n_prn", C.c_uint32), ("n_dopp", C.c_uint32), ("n_sets", C.c_uint32),
                 ("excl", C.c_uint32), ("block_len", C.c_uint32)]
@@ -70,6 +81,14 @@ _SIGS = {
                     _st),
     "gnss_refine_device": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_double, _P, _P], _st),
     "gnss_acquire_batch": ([_P, C.c_size_t, C.c_size_t, _P], _st),
+    "gnss_server_create": ([_P, C.POINTER(_P)], _st),
+    "gnss_server_destroy": ([_P], _st),
+    "gnss_submit": ([_P, C.POINTER(PlanDesc), _P, C.c_size_t, C.POINTER(C.c_uint64)], _st),
+    "gnss_poll": ([_P, C.c_uint64, _P, C.c_size_t, C.POINTER(C.c_size_t)], _st),
+    "gnss_wait": ([_P, C.c_uint64, C.c_uint32, _P, C.c_size_t, C.POINTER(C.c_size_t)], _st),
+    "gnss_cancel": ([_P, C.c_uint64], _st),
+    "gnss_server_get_stats": ([_P, _P], _st),
+    "gnss_server_inject_alloc_failure": ([_P, C.c_int], _st),
     "gnss_probe_ffma": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], _st),
     "gnss_last_error": ([], C.c_char_p),
 }
@@ -264,6 +283,67 @@ def acquire_batch(requests, scratch_budget: int = 0, stream=None) -> None:
         arr[k] = Request(plan.handle.value if hasattr(plan.handle, "value") else plan.handle, _ptr(smp), n,
                          _ptr(out), _ptr(surf))
     check(load().gnss_acquire_batch(arr, len(reqs), scratch_budget, _stream_ptr(stream)), "gnss_acquire_batch")
+
+
+class Server:
+    """Request server with continuous batching (gnss_server_*)."""
+
+    def __init__(self, device_mem_budget: int = 0, host_staging_bytes: int = 0, max_batch: int = 0,
+                 streams: int = 0, queue_timeout_ms: int = 0):
+        cfg = ServerConfig(device_mem_budget, host_staging_bytes, max_batch, streams, queue_timeout_ms, 0)
+        h = _P()
+        check(load().gnss_server_create(C.byref(cfg), C.byref(h)), "gnss_server_create")
+        self._h = h
+
+    @staticmethod
+    def desc_for(rec, prns=range(1, 33), threshold: float = 2.0) -> PlanDesc:
+        return PlanDesc(fs_hz=rec.fs, coh_ms=rec.coh_ms, noncoh=rec.noncoh, dopp_min_hz=rec.dopp_min_hz,
+                        dopp_step_hz=rec.dopp_step_hz, n_dopp=rec.n_dopp, prn_mask=prn_mask(prns),
+                        threshold=threshold, flags=HALF_BIT if rec.half_bit else 0, format=rec.fmt)
+
+    def submit(self, desc: PlanDesc, samples: np.ndarray, n_samples: int) -> int:
+        t = C.c_uint64()
+        samples = np.ascontiguousarray(samples)
+        check(load().gnss_submit(self._h, C.byref(desc), samples.ctypes.data, n_samples, C.byref(t)), "gnss_submit")
+        return t.value
+
+    def poll(self, ticket: int, cap: int = 32):
+        """Records (numpy) when done, None while pending; raises GnssError on failure."""
+        out = np.zeros(cap, DETECTION_DTYPE)
+        n = C.c_size_t()
+        st = load().gnss_poll(self._h, ticket, out.ctypes.data, cap, C.byref(n))
+        if st == EAGAIN:
+            return None
+        check(st, "gnss_poll")
+        return out[: min(n.value, cap)]
+
+    def wait(self, ticket: int, timeout_ms: int = 60000, cap: int = 32):
+        out = np.zeros(cap, DETECTION_DTYPE)
+        n = C.c_size_t()
+        check(load().gnss_wait(self._h, ticket, timeout_ms, out.ctypes.data, cap, C.byref(n)), "gnss_wait")
+        return out[: min(n.value, cap)]
+
+    def cancel(self, ticket: int) -> None:
+        check(load().gnss_cancel(self._h, ticket), "gnss_cancel")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(load().gnss_server_get_stats(self._h, C.byref(s)), "gnss_server_get_stats")
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_ if k != "reserved"}
+
+    def inject_alloc_failure(self, k: int) -> None:
+        check(load().gnss_server_inject_alloc_failure(self._h, k), "gnss_server_inject_alloc_failure")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gnss_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def candidates(prn, f_hz, tau_chips) -> np.ndarray:
