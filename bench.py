@@ -161,6 +161,138 @@ class ClockSampler:
         return out
 
 
+def make_workloads(args):
+    """All synthetic inputs, generated before any CUDA call (the process pool
+    uses spawn; a pool forked after CUDA initialisation can hang)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    rec = siggen.weak_100ms()
+    batch, serve = [], []
+    if not args.no_batch or not args.no_serve:
+        n = os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        with cf.ProcessPoolExecutor(max_workers=min(n, 32), mp_context=ctx) as ex:
+            if not args.no_batch:
+                chunks = [list(range(i, args.batch_requests, 8)) for i in range(8)]
+                parts = list(ex.map(siggen.batch_requests_subset, [(args.batch_requests, c) for c in chunks]))
+                by_idx = {}
+                for c, part in zip(chunks, parts):
+                    for i, r in zip(c, part):
+                        by_idx[i] = r
+                batch = [by_idx[i] for i in range(args.batch_requests)]
+            if not args.no_serve:
+                serve = siggen.serving_requests(args.serve_pool)
+    return rec, batch, serve
+
+
+def run_batch(g, torch, batch, stream, flush, steps):
+    """256 uneven recordings: one gnss_acquire_batch per step vs one
+    gnss_acquire_device per recording, recordings resident on the device."""
+    plans = {}
+    items = []
+    for r in batch:
+        key = (r.fs, r.coh_ms, r.dopp_min_hz, r.dopp_step_hz, r.n_dopp, r.fmt, r.half_bit)
+        if key not in plans:
+            plans[key] = g.Plan.for_recording(r)
+        plan = plans[key]
+        raw = torch.from_numpy(np.ascontiguousarray(r.raw)).cuda()
+        out = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+        items.append((plan, raw, r.n_samples, out, None))
+    cells = sum(_cells(p.n_prn, p.n_dopp, p.N, p.n_blocks(n), p.desc.coh_ms) for p, _, n, _, _ in items)
+
+    def batched():
+        g.acquire_batch(items, stream=stream)
+
+    def per_request():
+        for plan, raw, n, out, _ in items:
+            plan.acquire_device(raw, n, out, stream=stream)
+
+    res = {}
+    for name, fn in (("batched", batched), ("one_request_per_launch", per_request)):
+        with torch.cuda.stream(stream):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        res[name] = {"ms_per_batch": t, "cells_per_s": cells / (t * 1e-3), "requests_per_s": len(items) / (t * 1e-3)}
+    res["speedup"] = res["one_request_per_launch"]["ms_per_batch"] / res["batched"]["ms_per_batch"]
+    res["requests"] = len(items)
+    res["cells_per_batch"] = cells
+    res["workload"] = ("uneven recordings 20-200 ms, fs {2.048, 4.096, 8.192} MHz, 2-bit, 32 PRN, "
+                       "+-10 kHz at 250/500 Hz, coherent 500/step ms, all blocks")
+    return res
+
+
+def run_serving(g, serve, rate, seconds, seed=1309005205):
+    """Poisson arrivals at 'rate' requests/s for 'seconds' through
+    gnss_submit / gnss_poll; latency = submit -> result observed (host clock)."""
+    import threading
+    srv = g.Server(max_batch=64, streams=2)
+    descs = [g.Server.desc_for(r) for r in serve]
+    for d, r in zip(descs, serve):  # plans and code spectra resident before timing
+        srv.wait(srv.submit(d, r.raw, r.n_samples), 600000)
+    rng = np.random.default_rng(seed)
+    pending = {}
+    done = []
+    busy = 0
+    lock = threading.Lock()
+    stop = threading.Event()
+
+    def poller():
+        while not stop.is_set() or pending:
+            with lock:
+                items = list(pending.items())
+            for t, (t0, _) in items:
+                try:
+                    r = srv.poll(t)
+                except g.GnssError:
+                    r = "err"
+                if r is not None:
+                    with lock:
+                        pending.pop(t, None)
+                    done.append(time.perf_counter() - t0)
+            time.sleep(0.0002)
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t_start = time.perf_counter()
+    t_next = t_start
+    k = 0
+    while t_next - t_start < seconds:
+        now = time.perf_counter()
+        if now < t_next:
+            time.sleep(t_next - now)
+        r = serve[k % len(serve)]
+        try:
+            tk = srv.submit(descs[k % len(serve)], r.raw, r.n_samples)
+            with lock:
+                pending[tk] = (time.perf_counter(), k)
+        except g.GnssError:
+            busy += 1
+        k += 1
+        t_next += rng.exponential(1.0 / rate)
+    stop.set()
+    th.join(timeout=600)
+    t_total = time.perf_counter() - t_start
+    srv.close()
+    lat = np.array(done) * 1e3
+    return {"offered_req_per_s": rate, "seconds": seconds, "submitted": k, "refused_busy": busy,
+            "completed": len(done), "requests_per_s": len(done) / t_total,
+            "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+            "workload": "Poisson arrivals over %d pooled recordings 10-500 ms, fs up to 16.384 MHz, 2-bit, "
+                        "32 PRN, +-10 kHz at 250/500 Hz" % len(serve)}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -169,6 +301,7 @@ def _dist():
 
 
 def run_ours(args):
+    rec, batch, serve = make_workloads(args)
     import torch
     import paper_1309_0052_b300 as g
 
@@ -177,7 +310,6 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    rec = siggen.weak_100ms()
     plan = g.Plan.for_recording(rec, prns=range(1, 33))
     B = plan.n_blocks(rec.n_samples)
     P, D, N, coh = plan.n_prn, plan.n_dopp, plan.N, rec.coh_ms
@@ -277,6 +409,10 @@ def run_ours(args):
     }
     det_ok = int(det["detected"].sum())
     line["detected_prns"] = det_ok
+    if batch:
+        line["batch"] = run_batch(g, torch, batch, stream, flush, steps=3)
+    if serve:
+        line["serving"] = run_serving(g, serve, args.serve_rate, args.serve_seconds)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(rec, args)
     if ws > 1:
@@ -369,6 +505,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-requests", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-pool", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

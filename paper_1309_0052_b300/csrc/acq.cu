@@ -375,15 +375,17 @@ __device__ __forceinline__ void row_stats(const float (&a)[E], int j, int excl, 
 }
 
 // ---------------------------------------------------------------------------
-// K4: correlate.  One CTA per (PRN p, Doppler d), tile = d * P + p; loops
-// over the B blocks of Y[d], accumulating |R|^2 per set in registers.
+// K4: correlate.  One CTA per (PRN p, Doppler d), tile = d * P + p; CTAs that
+// share d are adjacent, so the spectra of one Doppler bin are read from L2
+// while they are hot.  The CTA runs its sets one after the other (with
+// half-bit sets: the even blocks, then the odd blocks), accumulating |R|^2
+// of the set in registers, so one accumulator serves both sets.
 // ---------------------------------------------------------------------------
-// One block: Y * conj(C_p) -> IFFT -> |.|^2 added to acc0 (even blocks) or,
-// with half-bit sets, to acc1 (odd blocks); one loop body serves both sets.
-template <int N, int E, bool DB, bool TWC, bool HALF>
+// One block: Y * conj(C_p) -> IFFT -> |.|^2 added to acc.
+template <int N, int E, bool DB, bool TWC>
 __device__ __forceinline__ void corr_block(const float2* __restrict__ y, const float2* __restrict__ cp, int j,
                                            float2* buf0, float2* buf1, int& phase, FftTw<N, E, true>& tw,
-                                           float (&acc0)[E], float (&acc1)[E], bool odd) {
+                                           float (&acc)[E]) {
   constexpr int T = N / E;
   if constexpr (TWC) tw.launder();
   // Re-read the code spectrum from L1 every block: hoisting these 16 loads
@@ -397,13 +399,8 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, const f
   }
   if constexpr (TWC) fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw);
   else fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
-  if (HALF && odd) {  // uniform across the CTA
 #pragma unroll
-    for (int r = 0; r < E; ++r) acc1[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc1[r]));
-  } else {
-#pragma unroll
-    for (int r = 0; r < E; ++r) acc0[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc0[r]));
-  }
+  for (int r = 0; r < E; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
 }
 
 // Per-PRN detection, run by the last CTA to finish a PRN (all its threads):
@@ -465,6 +462,7 @@ template <int N, bool HALF>
 __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2* sm) {
   constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
   constexpr bool DB = Cfg<N>::DB, TWC = Cfg<N>::TWC;
+  constexpr int S = HALF ? 2 : 1;
   float2* buf0 = sm;
   float2* buf1 = DB ? sm + FftShape<N>::smem_elems : sm;
   __shared__ float s_val[32];
@@ -475,30 +473,25 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   const float2* cp = a.cspec + (size_t)p * N;
   FftTw<N, E, true> tw;
   if constexpr (TWC) tw.init(j);
-  float acc0[E], acc1[E];
-#pragma unroll
-  for (int r = 0; r < E; ++r) acc0[r] = acc1[r] = 0.f;
   const float2* yd = a.Y + (size_t)d * a.B * N;
   int phase = 0;
-  for (int b = 0; b < a.B; ++b)
-    corr_block<N, E, DB, TWC, HALF>(yd + (size_t)b * N, cp, j, buf0, buf1, phase, tw, acc0, acc1, (b & 1) != 0);
-  // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
-  constexpr float sc = 1.f / ((float)N * (float)N);
+#pragma unroll 1
+  for (int set = 0; set < S; ++set) {
+    float acc[E];
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    acc0[r] *= sc;
-    acc1[r] *= sc;
-  }
-  constexpr int sets = HALF ? 2 : 1;
+    for (int r = 0; r < E; ++r) acc[r] = 0.f;
+    for (int b = set; b < a.B; b += S)
+      corr_block<N, E, DB, TWC>(yd + (size_t)b * N, cp, j, buf0, buf1, phase, tw, acc);
+    // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
+    constexpr float sc = 1.f / ((float)N * (float)N);
 #pragma unroll
-  for (int s = 0; s < sets; ++s) {
-    const float(&acc)[E] = (s == 0) ? acc0 : acc1;
+    for (int r = 0; r < E; ++r) acc[r] *= sc;
     if (a.surface != nullptr) {
-      float* row = a.surface + (((size_t)s * a.P + p) * a.D + d) * (size_t)N;
+      float* row = a.surface + (((size_t)set * a.P + p) * a.D + d) * (size_t)N;
 #pragma unroll
       for (int r = 0; r < E; ++r) row[j + T * r] = acc[r];
     }
-    row_stats<N, E>(acc, j, a.excl, s_val, s_idx, a.rows + ((size_t)s * a.P + p) * a.D + d);
+    row_stats<N, E>(acc, j, a.excl, s_val, s_idx, a.rows + ((size_t)set * a.P + p) * a.D + d);
   }
   // The last CTA of PRN p (of its D Doppler rows) runs the detection.
   __threadfence();
@@ -507,7 +500,7 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   __syncthreads();
   if (s_last) {
     __threadfence();
-    finalize_prn<N, T>(a, p, sets, s_val, s_idx);
+    finalize_prn<N, T>(a, p, S, s_val, s_idx);
   }
 }
 

@@ -128,12 +128,85 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
     for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
 }
 
+// a + w b with four FMAs.
+__device__ __forceinline__ float2 c_fma(float2 a, float2 w, float2 b) {
+  return make_float2(fmaf(w.x, b.x, fmaf(-w.y, b.y, a.x)), fmaf(w.x, b.y, fmaf(w.y, b.x, a.y)));
+}
+// 2 a - t (the other output of a butterfly whose first output t = a + u).
+__device__ __forceinline__ float2 c_twice_minus(float2 a, float2 t) {
+  return make_float2(fmaf(2.f, a.x, -t.x), fmaf(2.f, a.y, -t.y));
+}
+
+// 4-point DFT of (x0, y x1, y^2 x2, y^3 x3) in place, given y1 = y and
+// y2 = y^2, in FMA form:
+//   p0 = x0 + y2 x2,  p1 = x0 - y2 x2,  q0 = x1 + y2 x3,  q1 = x1 - y2 x3,
+//   X0 = p0 + y1 q0,  X2 = p0 - y1 q0,  X1 = p1 + W4 y1 q1,  X3 = p1 - W4 y1 q1
+// (W4 = -i forward, +i inverse); every difference is formed as 2a - (a + b).
+template <bool INV>
+__device__ __forceinline__ void dft4_tw(float2& x0, float2& x1, float2& x2, float2& x3, float2 y1, float2 y2) {
+  const float2 p0 = c_fma(x0, y2, x2);
+  const float2 p1 = c_twice_minus(x0, p0);
+  const float2 q0 = c_fma(x1, y2, x3);
+  const float2 q1 = c_twice_minus(x1, q0);
+  const float2 X0 = c_fma(p0, y1, q0);
+  const float2 X2 = c_twice_minus(p0, X0);
+  const float2 X1 = c_fma(p1, c_quarter<INV>(y1), q1);
+  const float2 X3 = c_twice_minus(p1, X1);
+  x0 = X0;
+  x1 = X1;
+  x2 = X2;
+  x3 = X3;
+}
+
+// Twiddled 16-point stage of a Stockham pass: X[t] = sum_s u[s] w^s W16^(s t)
+// with s = n2 + 4 n1, t = k1 + 4 k2:
+//   stage 1 (per n2): a[n2][k1] = DFT4 over n1 of u[n2 + 4 n1] (w^4)^n1,
+//   stage 2 (per k1): X[k1 + 4 k2] = DFT4 over n2 of a[n2][k1] z^n2,
+//                     z = w W16^k1,
+// both with dft4_tw; w1, w2, w4, w8 are w, w^2, w^4, w^8.  Natural order out.
+template <bool INV>
+__device__ __forceinline__ void dft16_tw(float2 (&v)[16], float2 w1, float2 w2, float2 w4, float2 w8) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4_tw<INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12], w4, w8);  // v[n2 + 4 k1]
+  dft4_tw<INV>(v[0], v[1], v[2], v[3], w1, w2);
+  dft4_tw<INV>(v[4], v[5], v[6], v[7], twiddle16<INV, 1>(w1), twiddle16<INV, 2>(w2));
+  dft4_tw<INV>(v[8], v[9], v[10], v[11], twiddle16<INV, 2>(w1), twiddle16<INV, 4>(w2));
+  dft4_tw<INV>(v[12], v[13], v[14], v[15], twiddle16<INV, 3>(w1), twiddle16<INV, 6>(w2));
+  float2 t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
+// The same without external twiddles (w = 1): stage 2 uses the constants
+// z = W16^k1.
+template <bool INV>
+__device__ __forceinline__ void dft16_c(float2 (&v)[16]) {
+  constexpr float sg = INV ? 1.f : -1.f;
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+  dft4<INV>(v[0], v[1], v[2], v[3]);
+  dft4_tw<INV>(v[4], v[5], v[6], v[7], make_float2(GNSS_C1, sg * GNSS_S1), make_float2(GNSS_R2, sg * GNSS_R2));
+  dft4_tw<INV>(v[8], v[9], v[10], v[11], make_float2(GNSS_R2, sg * GNSS_R2), make_float2(0.f, sg));
+  dft4_tw<INV>(v[12], v[13], v[14], v[15], make_float2(GNSS_S1, sg * GNSS_C1), make_float2(-GNSS_R2, sg * GNSS_R2));
+  float2 t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_r(float2 (&u)[R]) {
   if constexpr (R == 2) dft2<INV>(u[0], u[1]);
   else if constexpr (R == 4) dft4<INV>(u[0], u[1], u[2], u[3]);
   else if constexpr (R == 8) dft8<INV>(u);
-  else dft16<INV>(u);
+  else dft16_c<INV>(u);
 }
 
 // Padded shared-memory index (one spare slot every 16 elements).
@@ -170,14 +243,21 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[E], int j) {
       float sn, cs;
       sincospif(scale * float(k), &sn, &cs);
       const float2 w = make_float2(cs, sn);
-      float2 wp = w;
+      if constexpr (R == 16) {
+        const float2 w2 = c_mul(w, w), w4 = c_mul(w2, w2), w8 = c_mul(w4, w4);
+        dft16_tw<INV>(u, w, w2, w4, w8);
+      } else {
+        float2 wp = w;
 #pragma unroll
-      for (int s = 1; s < R; ++s) {
-        u[s] = c_mul(u[s], wp);
-        if (s + 1 < R) wp = c_mul(wp, w);
+        for (int s = 1; s < R; ++s) {
+          u[s] = c_mul(u[s], wp);
+          if (s + 1 < R) wp = c_mul(wp, w);
+        }
+        dft_r<R, INV>(u);
       }
+    } else {
+      dft_r<R, INV>(u);
     }
-    dft_r<R, INV>(u);
 #pragma unroll
     for (int t = 0; t < R; ++t) v[q + Q * t] = u[t];
   }
@@ -256,6 +336,7 @@ __device__ __forceinline__ void fft_block(float2 (&v)[E], int j, float2* buf0, f
 // ---------------------------------------------------------------------------
 template <int R>
 struct TwBase {
+  static_assert(R < 16, "radix-16 passes use TwBase16");
   static constexpr int NA = R >= 4 ? 3 : 1;
   static constexpr int NB = R >= 8 ? R / 4 - 1 : 0;
   float2 a[NA];
@@ -298,6 +379,32 @@ struct TwBase {
   }
 };
 
+// Radix-16 passes keep w, w^2, w^4, w^8 for dft16_tw.
+struct TwBase16 {
+  float2 w1, w2, w4, w8;
+  __device__ __forceinline__ void init(float turns2) {
+    float sn, cs;
+    sincospif(turns2, &sn, &cs);
+    w1 = make_float2(cs, sn);
+    w2 = c_mul(w1, w1);
+    w4 = c_mul(w2, w2);
+    w8 = c_mul(w4, w4);
+  }
+  __device__ __forceinline__ void launder() {
+    asm volatile("" : "+f"(w1.x), "+f"(w1.y), "+f"(w2.x), "+f"(w2.y));
+    asm volatile("" : "+f"(w4.x), "+f"(w4.y), "+f"(w8.x), "+f"(w8.y));
+  }
+};
+
+template <int R>
+struct TwSel {
+  using type = TwBase<R>;
+};
+template <>
+struct TwSel<16> {
+  using type = TwBase16;
+};
+
 template <int R, int S, bool LAST>
 struct TwApply {
   __device__ __forceinline__ static void run(float2 (&u)[R], const TwBase<R>& t) {
@@ -312,7 +419,7 @@ struct FftTw {
   static constexpr int R = PassRadix<N, NS>::value;
   static constexpr int Q = E / R;
   static constexpr int T = N / E;
-  TwBase<R> tw[NS > 1 ? Q : 1];
+  typename TwSel<R>::type tw[NS > 1 ? Q : 1];
   FftTw<N, E, INV, NS * R> next;
 
   __device__ __forceinline__ void init(int j) {
@@ -347,8 +454,12 @@ __device__ __forceinline__ void pass_compute_tw(float2 (&v)[E], const FftTw<N, E
     float2 u[R];
 #pragma unroll
     for (int s = 0; s < R; ++s) u[s] = v[q + Q * s];
-    if constexpr (NS > 1) TwApply<R, 1, R == 2>::run(u, tw.tw[q]);
-    dft_r<R, INV>(u);
+    if constexpr (NS > 1 && R == 16) {
+      dft16_tw<INV>(u, tw.tw[q].w1, tw.tw[q].w2, tw.tw[q].w4, tw.tw[q].w8);
+    } else {
+      if constexpr (NS > 1) TwApply<R, 1, R == 2>::run(u, tw.tw[q]);
+      dft_r<R, INV>(u);
+    }
 #pragma unroll
     for (int t = 0; t < R; ++t) v[q + Q * t] = u[t];
   }

@@ -211,11 +211,8 @@ def weak_100ms(seed: int = SEED_BASE + 2) -> Recording:
                           half_bit=True)
 
 
-def batch_requests(n_req: int = 256, seed: int = SEED_BASE + 3, fs_choices=(2_048_000, 4_096_000, 8_192_000),
-                   ms_range=(20, 200), sats_range=(4, 10), cn0=(30.0, 48.0)) -> list:
-    """Batched workload: uneven recordings, 2-bit packed, each with its own
-    fs, length (integer ms), Doppler step in {250, 500} Hz over +-10 kHz and
-    coherent length 500 / step ms."""
+def _batch_params(n_req, seed, fs_choices, ms_range, sats_range):
+    """Per-request (fs, ms, step, n_sats, sub-seed), drawn in request order."""
     rng = np.random.Generator(np.random.PCG64(seed))
     params = []
     for _ in range(n_req):
@@ -225,14 +222,30 @@ def batch_requests(n_req: int = 256, seed: int = SEED_BASE + 3, fs_choices=(2_04
         nsat = int(rng.integers(sats_range[0], sats_range[1] + 1))
         sub = int(rng.integers(0, 2**31))
         params.append((fs, ms, step, nsat, sub))
-    reqs = []
-    for fs, ms, step, nsat, sub in params:
-        coh = 500 // step
-        n = fs // 1000 * ms
-        reqs.append(make_recording(sub, fs, n, FMT_2BIT_IQ, nsat, cn0, (-9500.0, 9500.0),
-                                   coh_ms=coh, dopp_min_hz=-10000, dopp_step_hz=step,
-                                   n_dopp=20000 // step + 1))
-    return reqs
+    return params
+
+
+def _batch_recording(p, cn0) -> Recording:
+    fs, ms, step, nsat, sub = p
+    coh = 500 // step
+    return make_recording(sub, fs, fs // 1000 * ms, FMT_2BIT_IQ, nsat, cn0, (-9500.0, 9500.0),
+                          coh_ms=coh, dopp_min_hz=-10000, dopp_step_hz=step, n_dopp=20000 // step + 1)
+
+
+def batch_requests(n_req: int = 256, seed: int = SEED_BASE + 3, fs_choices=(2_048_000, 4_096_000, 8_192_000),
+                   ms_range=(20, 200), sats_range=(4, 10), cn0=(30.0, 48.0)) -> list:
+    """Batched workload: uneven recordings, 2-bit packed, each with its own
+    fs, length (integer ms), Doppler step in {250, 500} Hz over +-10 kHz and
+    coherent length 500 / step ms."""
+    return [_batch_recording(p, cn0) for p in _batch_params(n_req, seed, fs_choices, ms_range, sats_range)]
+
+
+def batch_requests_subset(arg) -> list:
+    """Requests idx of batch_requests(n) with its default parameters, for
+    generation in parallel worker processes: arg = (n, idx)."""
+    n, idx = arg
+    params = _batch_params(n, SEED_BASE + 3, (2_048_000, 4_096_000, 8_192_000), (20, 200), (4, 10))
+    return [_batch_recording(params[i], (30.0, 48.0)) for i in idx]
 
 
 def refine_12ms(seed: int = SEED_BASE + 4) -> Recording:
