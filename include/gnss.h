@@ -400,6 +400,24 @@ GNSS_API gnss_status gnss_server_get_stats(gnss_server* srv, gnss_server_stats* 
  * carries on.  Nothing is faulted on the device. */
 GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
 
+/* Launch-shape autotuner of the correlate kernel (the FFT-heavy stage).  It
+ * can hold 16 or 32 FFT elements per thread (N/16 or N/32 threads per FFT;
+ * 32 needs N >= 1024, 16 needs N <= 16384).  With force_elems = 0 every valid
+ * choice is timed on a probe shaped like the plan (its Doppler bins up to 32,
+ * its sets, 8 blocks) and the fastest is recorded for the plan's FFT size on
+ * the current device; with force_elems = 16 or 32 that choice is recorded
+ * without timing.  Later launches of that FFT size (single, batched, served)
+ * use it.  Synchronous.  out may be NULL. */
+typedef struct {
+  uint32_t N;            /* FFT size tuned                             */
+  uint32_t n_variants;   /* variants timed                             */
+  uint32_t elems[4];     /* elements per thread of each timed variant  */
+  float ms[4];           /* median probe time of each (ms)             */
+  uint32_t chosen;       /* elements per thread now in use for N       */
+} gnss_tune_result;
+
+GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_elems, gnss_tune_result* out);
+
 /* FP32 FMA throughput probe (a measurement aid with no counterpart in the
  * paper; it states the ALU roof the acquisition kernels are held against):
  * 'iters' rounds of 128 dependent-chain FMAs per thread, 4 CTAs of 512

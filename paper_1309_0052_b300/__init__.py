@@ -48,6 +48,11 @@ class ServerStats(C.Structure):
                 ("reserved", C.c_uint32), ("device_bytes_reserved", C.c_size_t)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("N", C.c_uint32), ("n_variants", C.c_uint32), ("elems", C.c_uint32 * 4), ("ms", C.c_float * 4),
+                ("chosen", C.c_uint32)]
+
+
 class PlanInfo(C.Structure):
     _fields_ = [("N", C.c_uint32), ("n_prn", C.c_uint32), ("n_dopp", C.c_uint32), ("n_sets", C.c_uint32),
                 ("excl", C.c_uint32), ("block_len", C.c_uint32)]
@@ -89,6 +94,7 @@ _SIGS = {
     "gnss_cancel": ([_P, C.c_uint64], _st),
     "gnss_server_get_stats": ([_P, _P], _st),
     "gnss_server_inject_alloc_failure": ([_P, C.c_int], _st),
+    "gnss_autotune": ([_P, C.c_uint32, _P], _st),
     "gnss_probe_ffma": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], _st),
     "gnss_last_error": ([], C.c_char_p),
 }
@@ -214,6 +220,14 @@ class Plan:
         check(load().gnss_plan_code_spectra(self._h, _ptr(out), out.numel() * 4, _stream_ptr(stream)),
               "gnss_plan_code_spectra")
         return out
+
+    def autotune(self, force_elems: int = 0) -> dict:
+        """gnss_autotune: time (or force) the correlate kernel's elements per
+        thread for this plan's FFT size on the current device."""
+        r = TuneResult()
+        check(load().gnss_autotune(self._h, force_elems, C.byref(r)), "gnss_autotune")
+        return {"N": r.N, "chosen": r.chosen,
+                "timed": {int(r.elems[k]): float(r.ms[k]) for k in range(r.n_variants)}}
 
     def surface_shape(self):
         return (self.n_sets, self.n_prn, self.n_dopp, self.N)

@@ -63,6 +63,18 @@ struct Cfg {
   static constexpr int MINB = T <= 256 ? 2 : 1;
 };
 
+// Launch configuration of the correlate kernel with E elements per thread
+// (a tuning choice: 16 or 32, see xcorr_variant).
+template <int N, int E>
+struct XCfg {
+  static constexpr int T = N / E;
+  static constexpr bool TWC = (E == 16);                        // twiddle bases cached in registers
+  static constexpr size_t buf_bytes = sizeof(float2) * FftShape<N>::smem_elems;
+  static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
+  static constexpr size_t smem = (DB ? 2 : 1) * buf_bytes;
+  static constexpr int MINB = T <= 256 ? 2 : 1;
+};
+
 // ---------------------------------------------------------------------------
 // K1b: code spectra.  Thread j builds the replica samples j + T r directly
 // (c_s[m] = c[floor(m * 1023 / N)]) and transforms them in place.
@@ -458,10 +470,10 @@ __device__ __forceinline__ void finalize_prn(const XcorrArgs& a, int p, int sets
   if (threadIdx.x == 0) a.out[p] = rec;
 }
 
-template <int N, bool HALF>
+template <int N, int E, bool HALF>
 __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2* sm) {
-  constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
-  constexpr bool DB = Cfg<N>::DB, TWC = Cfg<N>::TWC;
+  constexpr int T = XCfg<N, E>::T;
+  constexpr bool DB = XCfg<N, E>::DB, TWC = XCfg<N, E>::TWC;
   constexpr int S = HALF ? 2 : 1;
   float2* buf0 = sm;
   float2* buf1 = DB ? sm + FftShape<N>::smem_elems : sm;
@@ -504,18 +516,18 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   }
 }
 
-template <int N, bool HALF>
-__global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB) k_xcorr(const XcorrArgs a) {
+template <int N, int E, bool HALF>
+__global__ void __launch_bounds__(XCfg<N, E>::T, XCfg<N, E>::MINB) k_xcorr(const XcorrArgs a) {
   extern __shared__ float2 sm[];
-  xcorr_tile<N, HALF>(a, blockIdx.x, sm);
+  xcorr_tile<N, E, HALF>(a, blockIdx.x, sm);
 }
 
-template <int N, bool HALF>
-__global__ void __launch_bounds__(Cfg<N>::T, Cfg<N>::MINB)
+template <int N, int E, bool HALF>
+__global__ void __launch_bounds__(XCfg<N, E>::T, XCfg<N, E>::MINB)
     k_xcorr_batch(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ base, int n) {
   extern __shared__ float2 sm[];
   const int r = find_request(base, n);
-  xcorr_tile<N, HALF>(reqs[r].xc, (int)(blockIdx.x - __ldg(base + r)), sm);
+  xcorr_tile<N, E, HALF>(reqs[r].xc, (int)(blockIdx.x - __ldg(base + r)), sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -581,19 +593,51 @@ cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const i
   GNSS_DISPATCH_N(s.N, return wipe_fft_n<NN>(s, d_samples, d_group, d_gkey, d_Z, d_Y, d_counters, stream));
 }
 
-template <int N>
-static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t stream) {
+// Correlate-kernel variant per device and FFT size: elements per thread E.
+static int g_xcorr_e[128][15];
+
+int xcorr_default_e(int N) { return N >= 16384 ? 32 : 16; }
+
+bool xcorr_valid_e(int N, int E) { return (E == 16 && N / 16 <= 1024) || (E == 32 && N >= 1024); }
+
+int xcorr_variant(int N) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int lg = 0;
+  while ((1 << lg) < N) ++lg;
+  const int e = (dev >= 0 && dev < 128 && lg < 15) ? __atomic_load_n(&g_xcorr_e[dev][lg], __ATOMIC_RELAXED) : 0;
+  return e ? e : xcorr_default_e(N);
+}
+
+void set_xcorr_variant(int N, int E) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int lg = 0;
+  while ((1 << lg) < N) ++lg;
+  if (dev >= 0 && dev < 128 && lg < 15) __atomic_store_n(&g_xcorr_e[dev][lg], E, __ATOMIC_RELAXED);
+}
+
+template <int N, int E>
+static cudaError_t xcorr_ne(const AcqShape& s, const XcorrArgs& a, cudaStream_t stream) {
   const int grid = s.P * s.D;
   if (s.sets == 2) {
-    cudaError_t e = set_smem(k_xcorr<N, true>, Cfg<N>::smem);
+    cudaError_t e = set_smem(k_xcorr<N, E, true>, XCfg<N, E>::smem);
     if (e != cudaSuccess) return e;
-    k_xcorr<N, true><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a);
+    k_xcorr<N, E, true><<<grid, XCfg<N, E>::T, XCfg<N, E>::smem, stream>>>(a);
   } else {
-    cudaError_t e = set_smem(k_xcorr<N, false>, Cfg<N>::smem);
+    cudaError_t e = set_smem(k_xcorr<N, E, false>, XCfg<N, E>::smem);
     if (e != cudaSuccess) return e;
-    k_xcorr<N, false><<<grid, Cfg<N>::T, Cfg<N>::smem, stream>>>(a);
+    k_xcorr<N, E, false><<<grid, XCfg<N, E>::T, XCfg<N, E>::smem, stream>>>(a);
   }
   return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t stream) {
+  if constexpr (N >= 1024) {
+    if (xcorr_variant(N) == 32) return xcorr_ne<N, 32>(s, a, stream);
+  }
+  return xcorr_ne<N, 16>(s, a, stream);
 }
 
 FoldArgs fold_args(const AcqShape& s, const uint8_t* d_samples, const int* d_gkey, float2* d_Z,
@@ -650,6 +694,19 @@ cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_c
   GNSS_DISPATCH_N(s.N, return xcorr_n<NN>(s, a, stream));
 }
 
+template <int N, int E>
+static cudaError_t xcorr_batch_ne(const BatchGroup& g, cudaStream_t stream) {
+  cudaError_t e;
+  if (g.sets == 2) {
+    if ((e = set_smem(k_xcorr_batch<N, E, true>, XCfg<N, E>::smem)) != cudaSuccess) return e;
+    k_xcorr_batch<N, E, true><<<g.xc_ctas, XCfg<N, E>::T, XCfg<N, E>::smem, stream>>>(g.reqs, g.xc_base, g.n);
+  } else {
+    if ((e = set_smem(k_xcorr_batch<N, E, false>, XCfg<N, E>::smem)) != cudaSuccess) return e;
+    k_xcorr_batch<N, E, false><<<g.xc_ctas, XCfg<N, E>::T, XCfg<N, E>::smem, stream>>>(g.reqs, g.xc_base, g.n);
+  }
+  return cudaGetLastError();
+}
+
 // Batched launches: every request of the group shares N, format and sets.
 template <int N>
 static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
@@ -662,14 +719,10 @@ static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
   if ((e = set_smem(k_carrier_fft_batch<N>, Cfg<N>::smem)) != cudaSuccess) return e;
   k_carrier_fft_batch<N><<<g.car_ctas, Cfg<N>::T, Cfg<N>::smem, stream>>>(g.reqs, g.car_base, g.n);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (g.sets == 2) {
-    if ((e = set_smem(k_xcorr_batch<N, true>, Cfg<N>::smem)) != cudaSuccess) return e;
-    k_xcorr_batch<N, true><<<g.xc_ctas, Cfg<N>::T, Cfg<N>::smem, stream>>>(g.reqs, g.xc_base, g.n);
-  } else {
-    if ((e = set_smem(k_xcorr_batch<N, false>, Cfg<N>::smem)) != cudaSuccess) return e;
-    k_xcorr_batch<N, false><<<g.xc_ctas, Cfg<N>::T, Cfg<N>::smem, stream>>>(g.reqs, g.xc_base, g.n);
+  if constexpr (N >= 1024) {
+    if (xcorr_variant(N) == 32) return xcorr_batch_ne<N, 32>(g, stream);
   }
-  return cudaGetLastError();
+  return xcorr_batch_ne<N, 16>(g, stream);
 }
 
 cudaError_t launch_batch(const BatchGroup& g, cudaStream_t stream) {

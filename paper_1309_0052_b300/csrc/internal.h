@@ -119,6 +119,12 @@ cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_c
                          cudaStream_t stream);
 bool supported_fft_size(int N);
 
+// Correlate-kernel variant (elements per thread E) per device and FFT size.
+int xcorr_variant(int N);
+int xcorr_default_e(int N);
+bool xcorr_valid_e(int N, int E);
+void set_xcorr_variant(int N, int E);
+
 // Fine acquisition (refine.cu).
 struct RefineJob {
   const uint8_t* samples;  // device recording, 16-byte aligned

@@ -1,0 +1,107 @@
+// tune.cu -- autotuner of the correlate kernel's launch shape.
+//
+// The correlate kernel (conj-multiply, IFFT, |.|^2, non-coherent sum) can
+// hold E = 16 or E = 32 FFT elements per thread: N / E threads per FFT,
+// different register budgets, occupancy and exchange costs.  Which one is
+// faster depends on the FFT size (and the GPU), so gnss_autotune times every
+// valid choice on a probe shaped like the plan and records the fastest for
+// that FFT size on the current device; every later launch (single or
+// batched) uses it.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+using namespace gnss;
+
+extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_elems, gnss_tune_result* out) {
+  if (!plan) return fail_status(GNSS_EINVAL, "NULL argument");
+  gnss_status st = check_plan_device(plan);
+  if (st != GNSS_OK) return st;
+  const int N = plan->N;
+  gnss_tune_result res;
+  memset(&res, 0, sizeof(res));
+  res.N = (uint32_t)N;
+  const int cand[2] = {16, 32};
+  if (force_elems) {
+    if (!xcorr_valid_e(N, (int)force_elems))
+      return fail_status(GNSS_EINVAL, "elements per thread must be 16 (N <= 16384) or 32 (N >= 1024)");
+    set_xcorr_variant(N, (int)force_elems);
+    res.chosen = force_elems;
+    if (out) *out = res;
+    return GNSS_OK;
+  }
+  // probe: the plan's Doppler bins (at most 32) and sets, 8 blocks of zeros
+  AcqShape s;
+  memset(&s, 0, sizeof(s));
+  s.fs = (int)plan->desc.fs_hz;
+  s.N = N;
+  s.coh = (int)plan->desc.coh_ms;
+  s.B = 8;
+  s.D = std::min(plan->D, 32);
+  s.G = 1;
+  s.P = plan->P;
+  s.sets = plan->sets;
+  s.excl = plan->excl;
+  s.threshold = plan->desc.threshold;
+  const AcqScratch lay = scratch_layout(s);
+  const size_t det = ((size_t)s.P * sizeof(gnss_detection) + 255) & ~(size_t)255;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_status(e, "cudaStreamCreate");
+  char* ws = nullptr;
+  st = scratch_alloc(plan->device, lay.total + det, cs, (void**)&ws);
+  if (st != GNSS_OK) {
+    cudaStreamDestroy(cs);
+    return st;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaMemsetAsync(ws, 0, lay.total + det, cs);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int prev = xcorr_variant(N);
+  float best = 0.f;
+  int best_e = prev;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    const int E = cand[k];
+    if (!xcorr_valid_e(N, E)) continue;
+    set_xcorr_variant(N, E);
+    std::vector<float> t;
+    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+      e = cudaMemsetAsync(ws + lay.counters, 0, sizeof(unsigned) * s.P, cs);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+      if (e == cudaSuccess)
+        e = launch_xcorr(s, reinterpret_cast<const float2*>(ws + lay.y), plan->d_cspec, plan->d_prns, nullptr,
+                         reinterpret_cast<RowStat*>(ws + lay.rows), reinterpret_cast<unsigned*>(ws + lay.counters),
+                         reinterpret_cast<gnss_detection*>(ws + lay.total), cs);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) t.push_back(ms);  // the first run warms up
+    }
+    if (e != cudaSuccess) break;
+    std::sort(t.begin(), t.end());
+    const float med = t[t.size() / 2];
+    res.elems[res.n_variants] = (uint32_t)E;
+    res.ms[res.n_variants] = med;
+    res.n_variants++;
+    if (best == 0.f || med < best) {
+      best = med;
+      best_e = E;
+    }
+  }
+  set_xcorr_variant(N, e == cudaSuccess ? best_e : prev);
+  res.chosen = (uint32_t)xcorr_variant(N);
+  cudaFreeAsync(ws, cs);
+  cudaStreamSynchronize(cs);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_status(e, "gnss_autotune");
+  if (out) *out = res;
+  return GNSS_OK;
+}
