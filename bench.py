@@ -398,7 +398,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": P * 28,
                 "p50_ms": float(np.percentile(e2e_ms, 50)), "p99_ms": float(np.percentile(e2e_ms, 99))},
         "gpu_launches": 3 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "k_xcorr<4096,half-bit>", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_xcorr<4096,16,half-bit>", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": traffic, "flops_per_launch": x_flops, "launch_ms": x_ms,
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 x max SM clock (of derived)",
