@@ -85,3 +85,51 @@ def test_oracle_and_cuda_path_share_no_code():
         if path.endswith((".py", ".c", ".h")):
             src = open(path).read()
             assert "paper_1309_0052_b300" not in src and "gnss.h" not in src and "csrc" not in src, path
+
+
+def test_host_side_rejections_of_later_entry_points(lib):
+    L = lib.lib
+    E = lib.EINVAL
+    assert L.gnss_refine(None, None, 0, 0, None, 1, 10, 10, 0.0, None, None) == E
+    assert L.gnss_refine_device(None, None, 0, None, 1, 10, 10, 0.0, None, None) == E
+    assert L.gnss_refine_eval(None, None, 0, 10, None, None, None, 1, None, None, None, None) == E
+    assert L.gnss_acquire_batch(None, 1, 0, None) == E
+    assert L.gnss_acquire_batch(None, 0, 0, None) == lib.OK  # empty batch
+    assert L.gnss_autotune(None, 0, None) == E
+    assert L.gnss_submit(None, None, None, 0, None) == E
+    assert L.gnss_poll(None, 1, None, 0, None) == E
+    assert L.gnss_wait(None, 1, 0, None, 0, None) == E
+    assert L.gnss_cancel(None, 1) == E
+    assert L.gnss_server_get_stats(None, None) == E
+    assert L.gnss_server_destroy(None) == lib.OK
+    fn = L.gnss_acquire_noalloc
+    fn.argtypes = [C.c_void_p] * 3 + [C.c_void_p] * 3
+    assert fn(None, None, 0, None, None, None) == E
+
+
+def test_record_layouts_match_the_header(lib, tmp_path):
+    """sizeof / offsetof of the header's records, compiled by gcc, equal the
+    binding's ctypes / numpy layouts."""
+    import subprocess
+    src = tmp_path / "sizes.c"
+    src.write_text(r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "gnss.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gnss_plan_desc), sizeof(gnss_detection),
+         sizeof(gnss_candidate), sizeof(gnss_refined), sizeof(gnss_request), sizeof(gnss_server_config),
+         sizeof(gnss_server_stats), sizeof(gnss_tune_result), sizeof(gnss_plan_info));
+  printf("%zu %zu %zu %zu\n", offsetof(gnss_detection, dopp_bin), offsetof(gnss_detection, ratio),
+         offsetof(gnss_refined, status), offsetof(gnss_plan_desc, prn_mask));
+  return 0;
+}
+""")
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    sizes, offs = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().splitlines()]
+    assert sizes == [C.sizeof(lib.PlanDesc), lib.DETECTION_DTYPE.itemsize, lib.CANDIDATE_DTYPE.itemsize,
+                     lib.REFINED_DTYPE.itemsize, C.sizeof(lib.Request), C.sizeof(lib.ServerConfig),
+                     C.sizeof(lib.ServerStats), C.sizeof(lib.TuneResult), C.sizeof(lib.PlanInfo)]
+    assert offs == [lib.DETECTION_DTYPE.fields["dopp_bin"][1], lib.DETECTION_DTYPE.fields["ratio"][1],
+                    lib.REFINED_DTYPE.fields["status"][1], lib.PlanDesc.prn_mask.offset]
