@@ -167,6 +167,7 @@ def make_workloads(args):
     import concurrent.futures as cf
     import multiprocessing as mp
     rec = siggen.weak_100ms()
+    long_rec = None if args.no_code_doppler else siggen.long_400ms()
     batch, serve = [], []
     if not args.no_batch or not args.no_serve:
         n = os.cpu_count() or 1
@@ -182,7 +183,7 @@ def make_workloads(args):
                 batch = [by_idx[i] for i in range(args.batch_requests)]
             if not args.no_serve:
                 serve = siggen.serving_requests(args.serve_pool)
-    return rec, batch, serve
+    return rec, batch, serve, long_rec
 
 
 def run_batch(g, torch, batch, stream, flush, steps):
@@ -232,6 +233,39 @@ def run_batch(g, torch, batch, stream, flush, steps):
     return res
 
 
+def run_code_doppler(g, torch, rec, stream, flush, steps):
+    """The 400 ms weak-signal request with and without code-Doppler
+    compensation (GNSS_CODE_DOPPLER): device time per request and the
+    satellites detected."""
+    raw = torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda()
+    res = {"workload": "long_400ms: fs 4.096 MHz, 400 ms 2-bit I/Q, 32 PRN x 81 Doppler (250 Hz) x 4096 phases, "
+                       "10 ms coh x 40 half-bit, 8 satellites at 27-36 dB-Hz",
+           "injected_prns": sorted(s.prn for s in rec.sats)}
+    for name, cd in (("plain", False), ("compensated", True)):
+        plan = g.Plan.for_recording(rec, code_doppler=cd)
+        B = plan.n_blocks(rec.n_samples)
+        cells = _cells(plan.n_prn, plan.n_dopp, plan.N, B, rec.coh_ms)
+        out = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(stream):
+            plan.acquire_device(raw, rec.n_samples, out, stream=stream)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                plan.acquire_device(raw, rec.n_samples, out, stream=stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        det = g.detections_from_bytes(out.cpu().numpy())
+        t = statistics.median(ms)
+        res[name] = {"ms_per_request": t, "cells_per_s": cells / (t * 1e-3),
+                     "detected_prns": sorted(int(d["prn"]) for d in det if d["detected"])}
+    return res
+
+
 def run_serving(g, serve, rate, seconds, seed=1309005205):
     """Poisson arrivals at 'rate' requests/s for 'seconds' through
     gnss_submit / gnss_poll; latency = submit -> result observed (host clock)."""
@@ -241,8 +275,10 @@ def run_serving(g, serve, rate, seconds, seed=1309005205):
     for d, r in zip(descs, serve):  # plans and code spectra resident before timing
         srv.wait(srv.submit(d, r.raw, r.n_samples), 600000)
     rng = np.random.default_rng(seed)
+    req_cells = [_cells(32, r.n_dopp, r.N, r.n_blocks, r.coh_ms) for r in serve]
     pending = {}
     done = []
+    done_cells = [0]
     busy = 0
     lock = threading.Lock()
     stop = threading.Event()
@@ -251,7 +287,7 @@ def run_serving(g, serve, rate, seconds, seed=1309005205):
         while not stop.is_set() or pending:
             with lock:
                 items = list(pending.items())
-            for t, (t0, _) in items:
+            for t, (t0, kk) in items:
                 try:
                     r = srv.poll(t)
                 except g.GnssError:
@@ -260,6 +296,7 @@ def run_serving(g, serve, rate, seconds, seed=1309005205):
                     with lock:
                         pending.pop(t, None)
                     done.append(time.perf_counter() - t0)
+                    done_cells[0] += req_cells[kk % len(serve)]
             time.sleep(0.0002)
 
     th = threading.Thread(target=poller, daemon=True)
@@ -287,10 +324,62 @@ def run_serving(g, serve, rate, seconds, seed=1309005205):
     lat = np.array(done) * 1e3
     return {"offered_req_per_s": rate, "seconds": seconds, "submitted": k, "refused_busy": busy,
             "completed": len(done), "requests_per_s": len(done) / t_total,
+            "cells_per_s": done_cells[0] / t_total,
             "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
             "workload": "Poisson arrivals over %d pooled recordings 10-500 ms, fs up to 16.384 MHz, 2-bit, "
                         "32 PRN, +-10 kHz at 250/500 Hz" % len(serve)}
+
+
+def run_cufft_comparator(g, torch, plan, raw_dev, n_samples, stream, flush, steps, ours_ms):
+    """Library comparison on the same GPU: this library's forward stage gives
+    the Doppler-bin spectra Y, then the correlate stage runs as a cuFFT
+    pipeline (torch.fft): Y x conj(C_p) for all PRNs at once, one batched
+    IFFT, |.|^2, the per-set block sums and the per-PRN surface maxima.
+    Timed with CUDA events like the native correlate launch it is set
+    against; also reports how far its surfaces are from the native ones."""
+    B = plan.n_blocks(n_samples)
+    P, D, N, S = plan.n_prn, plan.n_dopp, plan.N, plan.n_sets
+    Y = torch.empty((D, B, N, 2), dtype=torch.float32, device="cuda")
+    Cs = torch.empty((P, N, 2), dtype=torch.float32, device="cuda")
+    ours = torch.zeros((S, P, D, N), dtype=torch.float32, device="cuda")
+    out = torch.zeros(P * 28, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        plan.stage_wipe_fft(raw_dev, n_samples, B, Y, stream=stream)
+        plan.code_spectra(Cs, stream=stream)
+        plan.stage_correlate(Y, B, out, surface=ours, stream=stream)
+    torch.cuda.synchronize()
+    Yc = torch.view_as_complex(Y)
+    Cc = torch.view_as_complex(Cs).conj()
+
+    def correlate():
+        Z = Yc.unsqueeze(0) * Cc[:, None, None, :]          # [P, D, B, N]
+        R = torch.fft.ifft(Z, dim=-1)                        # cuFFT, 1/N scaled
+        pw = R.real.square() + R.imag.square()
+        surf = torch.stack([pw[:, :, s::S].sum(dim=2) for s in range(S)])  # [S, P, D, N]
+        peak = surf.flatten(2).max(dim=2)
+        return surf, peak
+
+    with torch.cuda.stream(stream):
+        surf, _ = correlate()
+    torch.cuda.synchronize()
+    err = float(((surf - ours).abs().amax(dim=(2, 3)) / ours.amax(dim=(2, 3))).max())
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            correlate()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    return {"kind": "cuFFT pipeline (torch.fft batched IFFT + torch elementwise/reductions) for the correlate "
+                    "stage, on this library's Doppler-bin spectra",
+            "correlate_ms": t, "native_correlate_ms": ours_ms, "native_speedup": t / ours_ms,
+            "cells_per_s_correlate_only": _cells(P, D, N, B, plan.desc.coh_ms) / (t * 1e-3),
+            "max_rel_surface_diff_vs_native": err}
 
 
 def reduce_max_over_ranks(value: float, device) -> float:
@@ -318,7 +407,7 @@ def _dist():
 
 
 def run_ours(args):
-    rec, batch, serve = make_workloads(args)
+    rec, batch, serve, long_rec = make_workloads(args)
     import torch
     import paper_1309_0052_b300 as g
 
@@ -422,10 +511,16 @@ def run_ours(args):
     }
     det_ok = int(det["detected"].sum())
     line["detected_prns"] = det_ok
+    if not args.no_cufft:
+        line["cufft_comparator"] = run_cufft_comparator(g, torch, plan, raw_dev, rec.n_samples, stream, flush,
+                                                        steps=10, ours_ms=x_ms)
+    if long_rec is not None:
+        line["code_doppler"] = run_code_doppler(g, torch, long_rec, stream, flush, steps=10)
     if batch:
         line["batch"] = run_batch(g, torch, batch, stream, flush, steps=3)
     if serve:
-        line["serving"] = run_serving(g, serve, args.serve_rate, args.serve_seconds)
+        line["serving"] = [run_serving(g, serve, float(r), args.serve_seconds)
+                           for r in args.serve_rates.split(",") if r.strip()]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(rec, args)
     if ws > 1:
@@ -457,12 +552,12 @@ def _load_traffic():
     return rec.get("dram_bytes_per_launch")
 
 
-def _oracle_sample(rec, threads):
-    """One bounded oracle step: every CPU_SAMPLE_EVERY-th Doppler bin of the
-    workload, all 32 PRNs, all blocks, both half-bit sets.  Returns cells."""
+def _oracle_sample(rec, threads, every=CPU_SAMPLE_EVERY):
+    """One bounded oracle step: every 'every'-th Doppler bin of the workload,
+    all 32 PRNs, all blocks, both half-bit sets.  Returns cells."""
     import oracle
     x = oracle.unpack(rec.raw, rec.n_samples, rec.fmt)
-    dopp = rec.dopp_hz[::CPU_SAMPLE_EVERY]
+    dopp = rec.dopp_hz[::every]
     S = oracle.surfaces(x, rec.fs, rec.coh_ms, rec.n_blocks, rec.half_bit, np.arange(1, 33), dopp, threads)
     oracle.detect(S, np.arange(1, 33))
     return _cells(32, len(dopp), rec.N, rec.n_blocks, rec.coh_ms)
@@ -477,9 +572,15 @@ def cpu_baseline(rec, args):
         cells += _oracle_sample(rec, threads)
         reps += 1
     dt = time.perf_counter() - t0
+    # one thread on a smaller sample (3 of 81 Doppler bins)
+    t1 = time.perf_counter()
+    cells1 = _oracle_sample(rec, 1, every=27)
+    dt1 = time.perf_counter() - t1
     return {"value": cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d x (27 of 81 Doppler bins, all 32 PRNs, 10 blocks, both sets), FP64 C oracle, "
-                      "%d threads over Doppler rows, %.1f s wall" % (reps, threads, dt)}
+                      "%d threads over Doppler rows, %.1f s wall" % (reps, threads, dt),
+            "single_thread": {"value": cells1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": "3 of 81 Doppler bins, all 32 PRNs, 10 blocks, both sets, %.1f s" % dt1}}
 
 
 def run_reference(args):
@@ -520,8 +621,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--no-code-doppler", action="store_true")
     ap.add_argument("--batch-requests", type=int, default=256)
-    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-rates", default="50,100,200",
+                    help="offered Poisson arrival rates (requests/s), one serving run each")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-pool", type=int, default=8)
     args = ap.parse_args()

@@ -69,6 +69,17 @@ typedef enum { GNSS_FMT_I8_IQ = 0, GNSS_FMT_2BIT_IQ = 1 } gnss_format;
 #define GNSS_HALF_BIT 0x1u     /* two non-coherent sets: even and odd blocks */
 #define GNSS_SECOND_WHOLE 0x2u /* second peak over the whole surface instead
                                   of the peak's Doppler row (needs a surface) */
+/* Code-Doppler compensation of the non-coherent sum.  The code NCO of the
+ * receiver (Section 3, Fig. 2) runs at the nominal chip rate, while a signal
+ * at Doppler f carries its code f / 1540 chips per second faster (1540
+ * carrier cycles per chip at L1), so over a long non-coherent sum its
+ * correlation peak walks by f t fs / f_L1 samples (f_L1 = 1540 x 1.023 MHz).
+ * With this flag, block b of bin f enters the sum circularly shifted by
+ *   sigma_b = floor(f b L / f_L1 + 1/2)  samples (exact integer arithmetic),
+ *   S[tau] += |R_b[(tau - sigma_b) mod N]|^2,
+ * so the peaks of all blocks line up on the code phase of block 0.  The paper
+ * does not treat code Doppler; without the flag no compensation is made. */
+#define GNSS_CODE_DOPPLER 0x4u
 
 /* Acquisition plan descriptor (Section 3, Fig. 2: sample rate and coherent
  * length set the replica loop length fs * T; Doppler grid and PRN set define
@@ -81,7 +92,7 @@ typedef enum { GNSS_FMT_I8_IQ = 0, GNSS_FMT_2BIT_IQ = 1 } gnss_format;
  *               (integer Hz; n_dopp >= 1, step >= 1 when n_dopp > 1)
  *  prn_mask     bit p-1 set = search PRN p (1..32); at least one bit
  *  threshold    detected = peak / second >= threshold (e.g. 2.0)
- *  flags        GNSS_HALF_BIT | GNSS_SECOND_WHOLE
+ *  flags        GNSS_HALF_BIT | GNSS_SECOND_WHOLE | GNSS_CODE_DOPPLER
  *  format       gnss_format of the recordings this plan will see */
 typedef struct {
   uint32_t fs_hz;
@@ -102,7 +113,8 @@ typedef struct {
  *  set        non-coherent set the record comes from (0, or 1 = odd blocks
  *             with GNSS_HALF_BIT; the set with the larger ratio, ties to 0)
  *  dopp_bin   index d of the peak, dopp_hz its frequency
- *  code_phase peak code phase in samples [0, N) (replica delay)
+ *  code_phase peak code phase in samples [0, N) (replica delay; with
+ *             GNSS_CODE_DOPPLER the delay of block 0)
  *  peak, second, ratio: surface values (sample units squared) and their ratio */
 typedef struct {
   uint8_t prn;
@@ -242,7 +254,9 @@ GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void* samples_d
  * one-stage-per-launch comparison.
  * gnss_stage_wipe_fft: carrier wipe-off, coherent fold and forward FFT of
  *   every (Doppler, block): spectra_dev = float [n_dopp][n_blocks][N][2],
- *   Y_{f,b} = FFT_N(y_{f,b}).  n_blocks <= floor(n_samples / L).
+ *   Y_{f,b} = FFT_N(y_{f,b}).  n_blocks <= floor(n_samples / L).  With
+ *   GNSS_CODE_DOPPLER, y_{f,b} is the block rotated by sigma_b samples
+ *   (y'[n] = y[(n - sigma_b) mod N]), which rotates its correlation alike.
  * gnss_stage_correlate: conj-multiply with every code spectrum, IFFT, |.|^2
  *   and the non-coherent sums over n_blocks blocks of spectra_dev; writes
  *   surface_dev (may be NULL) and the per-PRN detections (device). */

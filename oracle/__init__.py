@@ -61,7 +61,7 @@ def _L():
         _lib.orc_dft.argtypes = [P, P, i, i, P, P]
         _lib.orc_corr_direct.argtypes = [P, P, i64, i, i, i64, i, P, P, P]
         _lib.orc_corr_fft.argtypes = [P, P, i64, i, i, i64, i, P, P, P]
-        _lib.orc_surfaces.argtypes = [P, P, i64, i64, i, i, i, P, i, P, i, i, P]
+        _lib.orc_surfaces.argtypes = [P, P, i64, i64, i, i, i, P, i, P, i, i, i, P]
         _lib.orc_detect.argtypes = [P, i, i, i, i, i, i, d, P, P]
         _lib.orc_refine_eval.argtypes = [P, P, i64, d, P, d, d, P, P]
         _lib.orc_refine.argtypes = [P, P, i64, d, P, d, d, i, d, P]
@@ -167,9 +167,18 @@ def corr_fft(x, fs: int, coh: int, f: int, b: int, chips) -> np.ndarray:
     return rr + 1j * ri
 
 
+def code_doppler_shift(f: int, b: int, L: int) -> int:
+    """Code-Doppler shift of block b at Doppler f, in samples: the nearest
+    integer to f b L / f_L1 (halves up), f_L1 = 1540 x 1.023 MHz.  Computed
+    with Python integers (exact)."""
+    f_l1 = 1540 * 1023000
+    return (2 * int(f) * int(b) * int(L) + f_l1) // (2 * f_l1)
+
+
 def surfaces(x, fs: int, coh: int, nblocks: int, half_bit: bool, prns, dopp_hz,
-             nthreads: int = 1) -> np.ndarray:
-    """Non-coherent power surfaces, float64 [sets][P][D][N]."""
+             nthreads: int = 1, code_doppler: bool = False) -> np.ndarray:
+    """Non-coherent power surfaces, float64 [sets][P][D][N]; with code_doppler
+    block b enters as |R_b[(tau - sigma_b) mod N]|^2."""
     xr, xi = _split(x)
     N = fs // 1000
     prns = np.ascontiguousarray(prns, np.int32)
@@ -178,7 +187,7 @@ def surfaces(x, fs: int, coh: int, nblocks: int, half_bit: bool, prns, dopp_hz,
     surf = np.zeros((sets, len(prns), len(dopp), N), np.float64)
     rc = _L().orc_surfaces(_p(xr), _p(xi), len(xr), int(fs), int(coh), int(nblocks),
                            int(bool(half_bit)), _p(prns), len(prns), _p(dopp), len(dopp),
-                           int(nthreads), _p(surf))
+                           int(nthreads), int(bool(code_doppler)), _p(surf))
     if rc != 0:
         raise ValueError("bad surface arguments")
     return surf
@@ -207,7 +216,7 @@ def detect(surf: np.ndarray, prns, threshold: float = 2.0, excl: int | None = No
 
 def acquire(raw, n_samples: int, fmt: int, fs: int, coh: int, dopp_hz, prns,
             half_bit: bool = False, noncoh: int = 0, threshold: float = 2.0,
-            nthreads: int = 1, whole_surface: bool = False):
+            nthreads: int = 1, whole_surface: bool = False, code_doppler: bool = False):
     """Whole acquisition: unpack, surfaces over all whole blocks (or the first
     noncoh), detection.  Returns (detections, surfaces)."""
     x = unpack(raw, n_samples, fmt)
@@ -215,7 +224,7 @@ def acquire(raw, n_samples: int, fmt: int, fs: int, coh: int, dopp_hz, prns,
     B = n_samples // (coh * N)
     if noncoh:
         B = min(B, noncoh)
-    surf = surfaces(x, fs, coh, B, half_bit, prns, dopp_hz, nthreads)
+    surf = surfaces(x, fs, coh, B, half_bit, prns, dopp_hz, nthreads, code_doppler)
     det = detect(surf, prns, threshold, whole_surface=whole_surface)
     for d in det:
         d["dopp_hz"] = int(np.asarray(dopp_hz)[d["dopp_bin"]])

@@ -14,7 +14,8 @@
  *   - exact integer carrier-phase reduction (f*n mod fs),
  *   - a textbook iterative radix-2 FFT with per-stage cos/sin twiddles,
  *   - a direct O(N^2) DFT and a brute-force time-domain correlation,
- *   - power surfaces, peak / second-peak detection, and
+ *   - power surfaces (optionally code-Doppler compensated), peak /
+ *     second-peak detection, and
  *   - the coherent-power objective of fine acquisition, its analytic
  *     gradient and a gradient-ascent refinement.
  *
@@ -283,7 +284,7 @@ void orc_corr_fft(const double *xr, const double *xi, int64_t fs, int N,
 typedef struct {
   const double *xr, *xi;
   int64_t fs;
-  int N, coh, nblocks, half_bit, nprn, ndopp;
+  int N, coh, nblocks, half_bit, nprn, ndopp, code_doppler;
   const int64_t *dopp_hz;     /* [ndopp] */
   const double *code_re;      /* [nprn][N] FFT of the replica */
   const double *code_im;
@@ -292,9 +293,28 @@ typedef struct {
   pthread_mutex_t lock;
 } orc_surface_job;
 
+/* Code Doppler.  The receiver's code NCO (Section 3, Fig. 2) runs at the
+ * nominal chip rate R_c; a signal at Doppler f has its code compressed by the
+ * same factor as its carrier, f / f_L1, so its delay falls by f t / f_L1 of a
+ * second per second: f t fs / f_L1 samples after t seconds (f_L1 = 1540 R_c
+ * = 1575.42 MHz).  At the start of block b (t = b L / fs) that is f b L / f_L1
+ * samples; the shift used is the nearest integer, halves rounded up:
+ * floor((2 f b L + f_L1) / (2 f_L1)), in exact integer arithmetic. */
+static int64_t orc_code_doppler_shift(int64_t f, int64_t b, int64_t L) {
+  const int64_t f_l1 = 1540LL * 1023000LL;
+  const int64_t num = 2 * f * b * L + f_l1;
+  const int64_t den = 2 * f_l1;
+  int64_t q = num / den; /* C truncates toward zero */
+  if (num % den != 0 && num < 0) q -= 1;
+  return q;
+}
+
 /* S^{(s)}_{p,f}[tau] = sum over blocks b with set(b) = s of |R_{p,f,b}[tau]|^2,
- * set(b) = b mod 2 when half-bit sets are on, else 0 (one set).  Each Doppler
- * row is independent, so worker threads take whole rows. */
+ * set(b) = b mod 2 when half-bit sets are on, else 0 (one set).  With code
+ * Doppler compensation, block b enters shifted by its code-Doppler shift
+ * sigma_b: S[tau] += |R_b[(tau - sigma_b) mod N]|^2, so that a peak whose
+ * delay falls by sigma_b samples at block b is summed at its block-0 delay.
+ * Each Doppler row is independent, so worker threads take whole rows. */
 static void *orc_surface_worker(void *arg) {
   orc_surface_job *job = (orc_surface_job *)arg;
   int N = job->N;
@@ -323,7 +343,13 @@ static void *orc_surface_worker(void *arg) {
         orc_fft(zr, zi, N, 1);
         double *row = job->surf +
                       (((size_t)s * job->nprn + p) * job->ndopp + d) * (size_t)N;
-        for (int t = 0; t < N; ++t) row[t] += zr[t] * zr[t] + zi[t] * zi[t];
+        int64_t sigma = 0;
+        if (job->code_doppler)
+          sigma = orc_code_doppler_shift(job->dopp_hz[d], b, (int64_t)job->coh * N);
+        for (int t = 0; t < N; ++t) {
+          int64_t src = ((t - sigma) % N + N) % N;
+          row[t] += zr[src] * zr[src] + zi[src] * zi[src];
+        }
       }
     }
   }
@@ -341,7 +367,7 @@ static void *orc_surface_worker(void *arg) {
 int orc_surfaces(const double *xr, const double *xi, int64_t n_samples,
                  int64_t fs, int coh, int nblocks, int half_bit,
                  const int *prns, int nprn, const int64_t *dopp_hz, int ndopp,
-                 int nthreads, double *surf) {
+                 int nthreads, int code_doppler, double *surf) {
   if (fs % 1000) return -1;
   int N = (int)(fs / 1000);
   if (N < 1 || (N & (N - 1))) return -1;
@@ -368,6 +394,7 @@ int orc_surfaces(const double *xr, const double *xi, int64_t n_samples,
   job.coh = coh;
   job.nblocks = nblocks;
   job.half_bit = half_bit;
+  job.code_doppler = code_doppler;
   job.nprn = nprn;
   job.ndopp = ndopp;
   job.dopp_hz = dopp_hz;

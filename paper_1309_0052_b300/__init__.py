@@ -23,6 +23,7 @@ FMT_I8_IQ = 0
 FMT_2BIT_IQ = 1
 HALF_BIT = 0x1
 SECOND_WHOLE = 0x2
+CODE_DOPPLER = 0x4
 
 
 class PlanDesc(C.Structure):
@@ -79,6 +80,7 @@ _SIGS = {
     "gnss_recording_bytes": ([C.c_uint32, C.c_size_t], C.c_size_t),
     "gnss_acquire": ([_P, _P, C.c_size_t, C.c_int, _P, _P, _P], _st),
     "gnss_acquire_device": ([_P, _P, C.c_size_t, _P, _P, _P], _st),
+    "gnss_acquire_noalloc": ([_P, _P, C.c_size_t, _P, _P, _P], _st),
     "gnss_stage_wipe_fft": ([_P, _P, C.c_size_t, C.c_uint32, _P, _P], _st),
     "gnss_stage_correlate": ([_P, _P, C.c_uint32, _P, _P, _P], _st),
     "gnss_refine_eval": ([_P, _P, C.c_size_t, C.c_uint32, _P, _P, _P, C.c_size_t, _P, _P, _P, _P], _st),
@@ -170,11 +172,12 @@ class Plan:
 
     def __init__(self, fs_hz: int, coh_ms: int, dopp_min_hz: int, dopp_step_hz: int, n_dopp: int,
                  prns=range(1, 33), noncoh: int = 0, threshold: float = 2.0, half_bit: bool = False,
-                 second_whole: bool = False, fmt: int = FMT_2BIT_IQ):
+                 second_whole: bool = False, fmt: int = FMT_2BIT_IQ, code_doppler: bool = False):
         self.desc = PlanDesc(fs_hz=fs_hz, coh_ms=coh_ms, noncoh=noncoh, dopp_min_hz=dopp_min_hz,
                              dopp_step_hz=dopp_step_hz, n_dopp=n_dopp, prn_mask=prn_mask(prns),
                              threshold=threshold,
-                             flags=(HALF_BIT if half_bit else 0) | (SECOND_WHOLE if second_whole else 0),
+                             flags=((HALF_BIT if half_bit else 0) | (SECOND_WHOLE if second_whole else 0)
+                                    | (CODE_DOPPLER if code_doppler else 0)),
                              format=fmt)
         h = _P()
         check(load().gnss_plan_create(C.byref(self.desc), C.byref(h)), "gnss_plan_create")

@@ -244,11 +244,26 @@ __global__ void __launch_bounds__(FoldCfg<N>::T) k_fold_batch(const BatchReq* __
   fold_tile<N, FMT>(reqs[r].fold, (int)(blockIdx.x - __ldg(base + r)));
 }
 
+// Code-Doppler shift of block b of bin f (GNSS_CODE_DOPPLER), in samples:
+// sigma = floor(f b L / f_L1 + 1/2), f_L1 = 1540 x 1.023 MHz, as the floor of
+// (2 f b L + f_L1) / (2 f_L1) in exact 64-bit integer arithmetic.
+__device__ __forceinline__ int64_t code_doppler_sigma(int f, int b, int64_t L) {
+  constexpr int64_t kL1 = 1540LL * 1023000LL;
+  const int64_t num = 2 * (int64_t)f * b * L + kL1, den = 2 * kL1;
+  int64_t q = num / den;
+  if (num % den != 0 && num < 0) --q;
+  return q;
+}
+
 // k_carrier_fft: one CTA per (Doppler d, block b), tile = d * B + b.  Loads the
-// folded block of its group in the FFT's register layout (m = j + T r),
-// multiplies by the carrier exp(-j 2 pi ((f (bL + m)) mod fs) / fs) -- exact
-// integer phase for r = 0, then a rotation by T samples per r -- and runs
-// the forward FFT: Y_{f,b} = FFT_N(y_{f,b}).
+// folded block of its group in the FFT's register layout, multiplies by the
+// carrier exp(-j 2 pi ((f (bL + m)) mod fs) / fs) -- exact integer phase for
+// r = 0, then a rotation by T samples per r -- and runs the forward FFT:
+// Y_{f,b} = FFT_N(y_{f,b}).  Element n = j + T r holds sample m = (n + sh)
+// mod N of the block: sh = 0, or (-sigma_b) mod N with GNSS_CODE_DOPPLER
+// (the rotation y'[n] = y[(n - sigma_b) mod N]).  The carrier chain runs over
+// the unwrapped m' = n + sh < 2N; a wrapped sample m = m' - N sits N samples
+// earlier, so its carrier is the chain's value times exp(+j 2 pi f N / fs).
 template <int N>
 __device__ __forceinline__ void carrier_tile(const CarrierArgs& a, int tile, float2* sm) {
   constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
@@ -259,19 +274,26 @@ __device__ __forceinline__ void carrier_tile(const CarrierArgs& a, int tile, flo
   const int d = tile / B, b = tile % B;
   const int f = a.dopp_min + d * a.dopp_step;
   const float2* z = a.Z + ((size_t)a.group[d] * B + b) * N;
+  int sh = 0;
+  if (a.code_dopp) sh = (int)(((-code_doppler_sigma(f, b, (int64_t)coh * N)) % N + N) % N);
   const int64_t fr = (((int64_t)f % fs) + fs) % fs;
-  const int64_t r0 = (fr * ((int64_t)b * coh * N + j)) % fs;
+  const int64_t r0 = (fr * ((int64_t)b * coh * N + j + sh)) % fs;
   const int64_t rs = (fr * T) % fs;
+  const int64_t rw = (fr * N) % fs;
   const float inv_fs = 1.f / (float)fs;
-  float s0, c0, ss, sc;
+  float s0, c0, ss, sc, sw, cw;
   sincospif(-2.f * (float)r0 * inv_fs, &s0, &c0);
   sincospif(-2.f * (float)rs * inv_fs, &ss, &sc);
+  sincospif(2.f * (float)rw * inv_fs, &sw, &cw);
   float2 car = make_float2(c0, s0);
   const float2 step = make_float2(sc, ss);
+  const float2 unwrap = make_float2(cw, sw);
   float2 v[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) {
-    v[r] = c_mul(__ldg(z + j + T * r), car);
+    const int m = j + sh + T * r;
+    const bool wrapped = m >= N;
+    v[r] = c_mul(__ldg(z + (wrapped ? m - N : m)), wrapped ? c_mul(car, unwrap) : car);
     car = c_mul(car, step);
   }
   int phase = 0;
@@ -663,6 +685,7 @@ CarrierArgs carrier_args(const AcqShape& s, const int* d_group, const float2* d_
   a.B = s.B;
   a.dopp_min = s.dopp_min;
   a.dopp_step = s.dopp_step;
+  a.code_dopp = s.code_dopp;
   return a;
 }
 

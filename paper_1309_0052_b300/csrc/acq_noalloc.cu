@@ -100,6 +100,7 @@ extern "C" GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void
   s.dopp_step = (int)plan->desc.dopp_step_hz;
   s.format = (int)plan->desc.format;
   s.second_whole = (plan->desc.flags & GNSS_SECOND_WHOLE) ? 1 : 0;
+  s.code_dopp = (plan->desc.flags & GNSS_CODE_DOPPLER) ? 1 : 0;
   s.threshold = plan->desc.threshold;
   const AcqScratch lay = scratch_layout(s);
   if (lay.total > GNSS_NOALLOC_SCRATCH_BYTES) {

@@ -99,6 +99,7 @@ static AcqShape shape_of(const gnss_plan* plan, int B) {
   s.dopp_step = (int)plan->desc.dopp_step_hz;
   s.format = (int)plan->desc.format;
   s.second_whole = (plan->desc.flags & GNSS_SECOND_WHOLE) ? 1 : 0;
+  s.code_dopp = (plan->desc.flags & GNSS_CODE_DOPPLER) ? 1 : 0;
   s.threshold = plan->desc.threshold;
   return s;
 }
@@ -186,7 +187,7 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   if (fmax > INT32_MAX / 2 || (int64_t)d.dopp_min_hz < INT32_MIN / 2) return fail(GNSS_EINVAL, "Doppler grid out of range");
   if ((d.prn_mask & 0xFFFFFFFFull) == 0 || (d.prn_mask >> 32)) return fail(GNSS_EINVAL, "prn_mask must select PRNs within 1..32");
   if (d.format != GNSS_FMT_I8_IQ && d.format != GNSS_FMT_2BIT_IQ) return fail(GNSS_EINVAL, "unknown format");
-  if (d.flags & ~(GNSS_HALF_BIT | GNSS_SECOND_WHOLE)) return fail(GNSS_EINVAL, "unknown flags");
+  if (d.flags & ~(GNSS_HALF_BIT | GNSS_SECOND_WHOLE | GNSS_CODE_DOPPLER)) return fail(GNSS_EINVAL, "unknown flags");
   if (!(d.threshold >= 0.f) || isinf(d.threshold)) return fail(GNSS_EINVAL, "threshold must be finite and >= 0");
 
   gnss_plan* p = new (std::nothrow) gnss_plan;

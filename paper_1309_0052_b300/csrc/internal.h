@@ -34,6 +34,7 @@ struct AcqShape {
   int dopp_min;    // Hz
   int dopp_step;   // Hz
   int format;      // gnss_format
+  int code_dopp;   // GNSS_CODE_DOPPLER
   int second_whole;
   float threshold;
 };
@@ -68,6 +69,7 @@ struct CarrierArgs {
   const int* group;        // [D] fold group per Doppler bin
   float2* Y;               // [D][B][N]
   int fs, coh, B, dopp_min, dopp_step;
+  int code_dopp;           // GNSS_CODE_DOPPLER: rotate block b by sigma_b samples
 };
 
 // One request of a batched launch.

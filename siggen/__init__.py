@@ -267,6 +267,18 @@ def refine_candidates(rec: Recording, n_random: int = 1000, seed: int = SEED_BAS
     return prn, f, tau
 
 
+def long_400ms(seed: int = SEED_BASE + 6) -> Recording:
+    """Long weak-signal request where code Doppler matters: fs 4.096 MHz,
+    400 ms 2-bit packed I/Q (819,200 bytes), 81 Doppler bins of 250 Hz over
+    +-10 kHz, 10 ms coherent x 40 blocks with half-bit sets, 8 satellites at
+    C/N0 27-36 dB-Hz, Doppler in +-9.5 kHz (up to 2.5 chips of code walk over
+    the recording), Doppler rate 0.5 Hz/s."""
+    return make_recording(seed, 4_096_000, 1_638_400, FMT_2BIT_IQ, 8, (27.0, 36.0),
+                          (-9500.0, 9500.0), rate=0.5,
+                          coh_ms=10, dopp_min_hz=-10000, dopp_step_hz=250, n_dopp=81,
+                          half_bit=True)
+
+
 def serving_requests(n_req: int, seed: int = SEED_BASE + 5, ms_range=(10, 500),
                      fs_choices=(2_048_000, 4_096_000, 8_192_000, 16_384_000)) -> list:
     """Serving workload: recordings 10-500 ms, fs in {2.048 .. 16.384} MHz,
