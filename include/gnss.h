@@ -192,7 +192,9 @@ GNSS_API size_t gnss_recording_bytes(uint32_t format, size_t n_samples);
  *                     has synchronised (a NULL stream is synchronised before
  *                     the call returns)
  * Errors: GNSS_EINVAL (n_samples < L, misaligned device pointer, NULL
- * arguments), GNSS_ENOMEM, GNSS_ECUDA. */
+ * arguments), GNSS_ENOMEM, GNSS_ECUDA; with a NULL stream also
+ * GNSS_ETIMEOUT when a bounded wait inside the staged correlate kernel gave
+ * up since the last such check (the records are then not valid). */
 GNSS_API gnss_status gnss_acquire(gnss_plan* plan, const void* samples, size_t n_samples, int samples_on_device,
                          gnss_detection* out, float* surface_dev, void* stream);
 
@@ -416,18 +418,24 @@ GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
 
 /* Launch-shape autotuner of the correlate kernel (the FFT-heavy stage).  It
  * can hold 16 or 32 FFT elements per thread (N/16 or N/32 threads per FFT;
- * 32 needs N >= 1024, 16 needs N <= 16384).  With force_elems = 0 every valid
- * choice is timed on a probe shaped like the plan (its Doppler bins up to 32,
- * its sets, 8 blocks) and the fastest is recorded for the plan's FFT size on
- * the current device; with force_elems = 16 or 32 that choice is recorded
- * without timing.  Later launches of that FFT size (single, batched, served)
- * use it.  Synchronous.  out may be NULL. */
+ * 32 needs N >= 1024, 16 needs N <= 16384), and with 16 it can stage the
+ * next block's spectrum into shared memory by a bulk TMA copy while the
+ * current block is transformed (variant code 16 | GNSS_TUNE_STAGED, offered
+ * where the CTA's shared memory still fits: N <= 8192).  With
+ * force_elems = 0 every valid variant is timed on a probe shaped like the
+ * plan (its Doppler bins up to 32, its sets, 8 blocks) and the fastest is
+ * recorded for the plan's FFT size on the current device; with force_elems
+ * = a variant code that variant is recorded without timing (GNSS_EINVAL if
+ * it is not valid for N).  Later launches of that FFT size (single, batched,
+ * served) use it.  Synchronous.  out may be NULL. */
+#define GNSS_TUNE_STAGED 0x100u
 typedef struct {
-  uint32_t N;            /* FFT size tuned                             */
-  uint32_t n_variants;   /* variants timed                             */
-  uint32_t elems[4];     /* elements per thread of each timed variant  */
-  float ms[4];           /* median probe time of each (ms)             */
-  uint32_t chosen;       /* elements per thread now in use for N       */
+  uint32_t N;            /* FFT size tuned                                */
+  uint32_t n_variants;   /* variants timed                                */
+  uint32_t elems[4];     /* variant code of each timed variant: elements  */
+                         /* per thread, | GNSS_TUNE_STAGED when staged    */
+  float ms[4];           /* median probe time of each (ms)                */
+  uint32_t chosen;       /* variant code now in use for N                 */
 } gnss_tune_result;
 
 GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_elems, gnss_tune_result* out);

@@ -64,15 +64,24 @@ struct Cfg {
 };
 
 // Launch configuration of the correlate kernel with E elements per thread
-// (a tuning choice: 16 or 32, see xcorr_variant).
-template <int N, int E>
+// (a tuning choice: 16 or 32, see xcorr_variant).  With ST the next block's
+// spectrum is staged into shared memory by a bulk TMA copy (N * 8 bytes more).
+template <int N, int E, bool ST = false>
 struct XCfg {
   static constexpr int T = N / E;
   static constexpr bool TWC = (E == 16);                        // twiddle bases cached in registers
   static constexpr size_t buf_bytes = sizeof(float2) * FftShape<N>::smem_elems;
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
-  static constexpr size_t smem = (DB ? 2 : 1) * buf_bytes;
+  static constexpr size_t stage_off = (DB ? 2 : 1) * buf_bytes;
+  static constexpr size_t smem = stage_off + (ST ? sizeof(float2) * N : 0);
   static constexpr int MINB = T <= 256 ? 2 : 1;
+  static_assert(stage_off % 16 == 0, "bulk copies need a 16-byte aligned destination");
+};
+
+// Staging is offered with 16 elements per thread when the CTA still fits.
+template <int N>
+struct StageFits {
+  static constexpr bool value = XCfg<N, 16, true>::smem <= 227 * 1024;
 };
 
 // ---------------------------------------------------------------------------
@@ -83,7 +92,7 @@ template <int N>
 __global__ void __launch_bounds__(Cfg<N>::T) k_code_spectra(const int8_t* __restrict__ codes,
                                                            float2* __restrict__ cspec) {
   constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   float2* buf0 = sm;
   float2* buf1 = Cfg<N>::DB ? sm + FftShape<N>::smem_elems : sm;
   const int p = blockIdx.x, j = threadIdx.x;
@@ -305,14 +314,14 @@ __device__ __forceinline__ void carrier_tile(const CarrierArgs& a, int tile, flo
 
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::T) k_carrier_fft(const CarrierArgs a) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   carrier_tile<N>(a, blockIdx.x, sm);
 }
 
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::T) k_carrier_fft_batch(const BatchReq* __restrict__ reqs,
                                                                 const uint32_t* __restrict__ base, int n) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int r = find_request(base, n);
   carrier_tile<N>(reqs[r].car, (int)(blockIdx.x - __ldg(base + r)), sm);
 }
@@ -409,30 +418,98 @@ __device__ __forceinline__ void row_stats(const float (&a)[E], int j, int excl, 
 }
 
 // ---------------------------------------------------------------------------
+// TMA staging of the next block's spectrum (the staged correlate variant):
+// one thread issues a bulk copy (cp.async.bulk) of the N-point row into a
+// shared-memory stage, completing on an mbarrier, while the CTA transforms
+// the current block; the CTA waits on the barrier's phase before it reads
+// the stage.  Every wait is bounded: one that gives up is counted in
+// g_stage_timeouts (read back by the synchronous entry point) and the
+// kernel runs on to its end.
+// ---------------------------------------------------------------------------
+__device__ unsigned g_stage_timeouts;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void stage_init(uint64_t* mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread: the stage's previous contents were read by every thread before
+// a CTA barrier that this thread has passed; order those generic-proxy reads
+// before the async-proxy writes, then arm the barrier and copy.
+__device__ __forceinline__ void stage_issue(float2* stg, const float2* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(stg)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+struct StageIssue {
+  float2* stg;
+  const float2* src;  // nullptr: no next block
+  uint64_t* mbar;
+  uint32_t bytes;
+  int j;
+  __device__ __forceinline__ void operator()() const {
+    if (j == 0 && src != nullptr) stage_issue(stg, src, bytes, mbar);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // K4: correlate.  One CTA per (PRN p, Doppler d), tile = d * P + p; CTAs that
 // share d are adjacent, so the spectra of one Doppler bin are read from L2
 // while they are hot.  The CTA runs its sets one after the other (with
 // half-bit sets: the even blocks, then the odd blocks), accumulating |R|^2
 // of the set in registers, so one accumulator serves both sets.
 // ---------------------------------------------------------------------------
-// One block: Y * conj(C_p) -> IFFT -> |.|^2 added to acc.
-template <int N, int E, bool DB, bool TWC>
+// One block: Y * conj(C_p) -> IFFT -> |.|^2 added to acc.  Without staging
+// Y is read from L2; with staging it is read from the shared-memory stage
+// (once the stage's barrier phase has completed) and the copy of the next
+// block is issued after the IFFT's first barrier.
+template <int N, int E, bool DB, bool TWC, bool ST>
 __device__ __forceinline__ void corr_block(const float2* __restrict__ y, const float2* __restrict__ cp, int j,
                                            float2* buf0, float2* buf1, int& phase, FftTw<N, E, true>& tw,
-                                           float (&acc)[E]) {
+                                           float (&acc)[E], const StageIssue& next, uint32_t& parity,
+                                           bool& stage_ok) {
   constexpr int T = N / E;
   if constexpr (TWC) tw.launder();
   // Re-read the code spectrum from L1 every block: hoisting these 16 loads
   // out of the block loop would pin 32 registers and force spills.
   asm volatile("" : "+l"(cp));
   float2 v[E];
+  if constexpr (ST) {
+    if (!stage_wait(next.mbar, parity)) stage_ok = false;
+    parity ^= 1u;
+    const float2* stg = next.stg;
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    // Y streams from L2 (not kept in L1); the code spectrum stays L1-resident
-    v[r] = c_mulconj(__ldcg(y + j + T * r), __ldg(cp + j + T * r));
+    for (int r = 0; r < E; ++r) v[r] = c_mulconj(stg[j + T * r], __ldg(cp + j + T * r));
+    fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw, next);
+  } else {
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      // Y streams from L2 (not kept in L1); the code spectrum stays L1-resident
+      v[r] = c_mulconj(__ldcg(y + j + T * r), __ldg(cp + j + T * r));
+    }
+    if constexpr (TWC) fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw);
+    else fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
   }
-  if constexpr (TWC) fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw);
-  else fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
 #pragma unroll
   for (int r = 0; r < E; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
 }
@@ -492,30 +569,54 @@ __device__ __forceinline__ void finalize_prn(const XcorrArgs& a, int p, int sets
   if (threadIdx.x == 0) a.out[p] = rec;
 }
 
-template <int N, int E, bool HALF>
+template <int N, int E, bool HALF, bool ST>
 __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2* sm) {
-  constexpr int T = XCfg<N, E>::T;
-  constexpr bool DB = XCfg<N, E>::DB, TWC = XCfg<N, E>::TWC;
+  using X = XCfg<N, E, ST>;
+  constexpr int T = X::T;
+  constexpr bool DB = X::DB, TWC = X::TWC;
   constexpr int S = HALF ? 2 : 1;
+  static_assert(!ST || TWC, "staging is built with cached twiddles");
   float2* buf0 = sm;
   float2* buf1 = DB ? sm + FftShape<N>::smem_elems : sm;
   __shared__ float s_val[32];
   __shared__ uint32_t s_idx[32];
   __shared__ unsigned s_last;
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ int s_stage_fail;
   const int j = threadIdx.x;
   const int p = tile % a.P, d = tile / a.P;
   const float2* cp = a.cspec + (size_t)p * N;
+  const float2* yd = a.Y + (size_t)d * a.B * N;
+  StageIssue next{reinterpret_cast<float2*>(reinterpret_cast<char*>(sm) + X::stage_off), nullptr, &s_mbar,
+                  (uint32_t)(sizeof(float2) * N), j};
+  uint32_t parity = 0;
+  bool stage_ok = true;
+  if constexpr (ST) {
+    if (j == 0) {
+      s_stage_fail = 0;
+      stage_init(&s_mbar);
+    }
+    __syncthreads();
+    if (j == 0) stage_issue(next.stg, yd, next.bytes, &s_mbar);  // block 0 of set 0
+  }
   FftTw<N, E, true> tw;
   if constexpr (TWC) tw.init(j);
-  const float2* yd = a.Y + (size_t)d * a.B * N;
   int phase = 0;
 #pragma unroll 1
   for (int set = 0; set < S; ++set) {
     float acc[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) acc[r] = 0.f;
-    for (int b = set; b < a.B; b += S)
-      corr_block<N, E, DB, TWC>(yd + (size_t)b * N, cp, j, buf0, buf1, phase, tw, acc);
+    for (int b = set; b < a.B; b += S) {
+      if constexpr (ST) {
+        // the block after b: the next of this set, else the first of the next set
+        int nb = b + S;
+        if (nb >= a.B) nb = set + 1 < S ? set + 1 : a.B;
+        next.src = nb < a.B ? yd + (size_t)nb * N : nullptr;
+      }
+      corr_block<N, E, DB, TWC, ST>(yd + (size_t)b * N, cp, j, buf0, buf1, phase, tw, acc, next, parity,
+                                    stage_ok);
+    }
     // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
     constexpr float sc = 1.f / ((float)N * (float)N);
 #pragma unroll
@@ -526,6 +627,16 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
       for (int r = 0; r < E; ++r) row[j + T * r] = acc[r];
     }
     row_stats<N, E>(acc, j, a.excl, s_val, s_idx, a.rows + ((size_t)set * a.P + p) * a.D + d);
+  }
+  if constexpr (ST) {
+    // A wait that gave up may leave a copy in flight: wait for it once more
+    // (bounded) before the CTA's shared memory is released.
+    if (!stage_ok) s_stage_fail = 1;
+    __syncthreads();
+    if (j == 0 && s_stage_fail) {
+      atomicAdd(&g_stage_timeouts, 1u);
+      stage_wait(&s_mbar, parity ^ 1u);
+    }
   }
   // The last CTA of PRN p (of its D Doppler rows) runs the detection.
   __threadfence();
@@ -538,18 +649,18 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   }
 }
 
-template <int N, int E, bool HALF>
+template <int N, int E, bool HALF, bool ST>
 __global__ void __launch_bounds__(XCfg<N, E>::T, XCfg<N, E>::MINB) k_xcorr(const XcorrArgs a) {
-  extern __shared__ float2 sm[];
-  xcorr_tile<N, E, HALF>(a, blockIdx.x, sm);
+  extern __shared__ __align__(16) float2 sm[];
+  xcorr_tile<N, E, HALF, ST>(a, blockIdx.x, sm);
 }
 
-template <int N, int E, bool HALF>
+template <int N, int E, bool HALF, bool ST>
 __global__ void __launch_bounds__(XCfg<N, E>::T, XCfg<N, E>::MINB)
     k_xcorr_batch(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ base, int n) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int r = find_request(base, n);
-  xcorr_tile<N, E, HALF>(reqs[r].xc, (int)(blockIdx.x - __ldg(base + r)), sm);
+  xcorr_tile<N, E, HALF, ST>(reqs[r].xc, (int)(blockIdx.x - __ldg(base + r)), sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,12 +726,29 @@ cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const i
   GNSS_DISPATCH_N(s.N, return wipe_fft_n<NN>(s, d_samples, d_group, d_gkey, d_Z, d_Y, d_counters, stream));
 }
 
-// Correlate-kernel variant per device and FFT size: elements per thread E.
+// Correlate-kernel variant per device and FFT size: elements per thread E,
+// plus GNSS_TUNE_STAGED for the TMA-staged form.
 static int g_xcorr_e[128][15];
 
 int xcorr_default_e(int N) { return N >= 16384 ? 32 : 16; }
 
-bool xcorr_valid_e(int N, int E) { return (E == 16 && N / 16 <= 1024) || (E == 32 && N >= 1024); }
+static bool stage_fits(int N) {
+  switch (N) {
+    case 256: return StageFits<256>::value;
+    case 512: return StageFits<512>::value;
+    case 1024: return StageFits<1024>::value;
+    case 2048: return StageFits<2048>::value;
+    case 4096: return StageFits<4096>::value;
+    case 8192: return StageFits<8192>::value;
+    case 16384: return StageFits<16384>::value;
+    default: return false;
+  }
+}
+
+bool xcorr_valid_e(int N, int code) {
+  if (code == (16 | (int)GNSS_TUNE_STAGED)) return N / 16 <= 1024 && stage_fits(N);
+  return (code == 16 && N / 16 <= 1024) || (code == 32 && N >= 1024);
+}
 
 int xcorr_variant(int N) {
   int dev = 0;
@@ -639,27 +767,32 @@ void set_xcorr_variant(int N, int E) {
   if (dev >= 0 && dev < 128 && lg < 15) __atomic_store_n(&g_xcorr_e[dev][lg], E, __ATOMIC_RELAXED);
 }
 
-template <int N, int E>
+template <int N, int E, bool ST>
 static cudaError_t xcorr_ne(const AcqShape& s, const XcorrArgs& a, cudaStream_t stream) {
+  using X = XCfg<N, E, ST>;
   const int grid = s.P * s.D;
   if (s.sets == 2) {
-    cudaError_t e = set_smem(k_xcorr<N, E, true>, XCfg<N, E>::smem);
+    cudaError_t e = set_smem(k_xcorr<N, E, true, ST>, X::smem);
     if (e != cudaSuccess) return e;
-    k_xcorr<N, E, true><<<grid, XCfg<N, E>::T, XCfg<N, E>::smem, stream>>>(a);
+    k_xcorr<N, E, true, ST><<<grid, X::T, X::smem, stream>>>(a);
   } else {
-    cudaError_t e = set_smem(k_xcorr<N, E, false>, XCfg<N, E>::smem);
+    cudaError_t e = set_smem(k_xcorr<N, E, false, ST>, X::smem);
     if (e != cudaSuccess) return e;
-    k_xcorr<N, E, false><<<grid, XCfg<N, E>::T, XCfg<N, E>::smem, stream>>>(a);
+    k_xcorr<N, E, false, ST><<<grid, X::T, X::smem, stream>>>(a);
   }
   return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t stream) {
+  const int v = xcorr_variant(N);
   if constexpr (N >= 1024) {
-    if (xcorr_variant(N) == 32) return xcorr_ne<N, 32>(s, a, stream);
+    if (v == 32) return xcorr_ne<N, 32, false>(s, a, stream);
   }
-  return xcorr_ne<N, 16>(s, a, stream);
+  if constexpr (StageFits<N>::value) {
+    if (v == (16 | (int)GNSS_TUNE_STAGED)) return xcorr_ne<N, 16, true>(s, a, stream);
+  }
+  return xcorr_ne<N, 16, false>(s, a, stream);
 }
 
 FoldArgs fold_args(const AcqShape& s, const uint8_t* d_samples, const int* d_gkey, float2* d_Z,
@@ -717,15 +850,16 @@ cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_c
   GNSS_DISPATCH_N(s.N, return xcorr_n<NN>(s, a, stream));
 }
 
-template <int N, int E>
+template <int N, int E, bool ST>
 static cudaError_t xcorr_batch_ne(const BatchGroup& g, cudaStream_t stream) {
+  using X = XCfg<N, E, ST>;
   cudaError_t e;
   if (g.sets == 2) {
-    if ((e = set_smem(k_xcorr_batch<N, E, true>, XCfg<N, E>::smem)) != cudaSuccess) return e;
-    k_xcorr_batch<N, E, true><<<g.xc_ctas, XCfg<N, E>::T, XCfg<N, E>::smem, stream>>>(g.reqs, g.xc_base, g.n);
+    if ((e = set_smem(k_xcorr_batch<N, E, true, ST>, X::smem)) != cudaSuccess) return e;
+    k_xcorr_batch<N, E, true, ST><<<g.xc_ctas, X::T, X::smem, stream>>>(g.reqs, g.xc_base, g.n);
   } else {
-    if ((e = set_smem(k_xcorr_batch<N, E, false>, XCfg<N, E>::smem)) != cudaSuccess) return e;
-    k_xcorr_batch<N, E, false><<<g.xc_ctas, XCfg<N, E>::T, XCfg<N, E>::smem, stream>>>(g.reqs, g.xc_base, g.n);
+    if ((e = set_smem(k_xcorr_batch<N, E, false, ST>, X::smem)) != cudaSuccess) return e;
+    k_xcorr_batch<N, E, false, ST><<<g.xc_ctas, X::T, X::smem, stream>>>(g.reqs, g.xc_base, g.n);
   }
   return cudaGetLastError();
 }
@@ -742,10 +876,27 @@ static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
   if ((e = set_smem(k_carrier_fft_batch<N>, Cfg<N>::smem)) != cudaSuccess) return e;
   k_carrier_fft_batch<N><<<g.car_ctas, Cfg<N>::T, Cfg<N>::smem, stream>>>(g.reqs, g.car_base, g.n);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int v = xcorr_variant(N);
   if constexpr (N >= 1024) {
-    if (xcorr_variant(N) == 32) return xcorr_batch_ne<N, 32>(g, stream);
+    if (v == 32) return xcorr_batch_ne<N, 32, false>(g, stream);
   }
-  return xcorr_batch_ne<N, 16>(g, stream);
+  if constexpr (StageFits<N>::value) {
+    if (v == (16 | (int)GNSS_TUNE_STAGED)) return xcorr_batch_ne<N, 16, true>(g, stream);
+  }
+  return xcorr_batch_ne<N, 16, false>(g, stream);
+}
+
+// Bounded waits of the staged correlate kernels that gave up since the last
+// call (the counter is reset).
+cudaError_t take_stage_timeouts(unsigned* count, cudaStream_t stream) {
+  unsigned zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(count, g_stage_timeouts, sizeof(unsigned), 0, cudaMemcpyDeviceToHost,
+                                            stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess && *count)
+    e = cudaMemcpyToSymbolAsync(g_stage_timeouts, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  return e;
 }
 
 cudaError_t launch_batch(const BatchGroup& g, cudaStream_t stream) {

@@ -159,6 +159,10 @@ static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_s
   if (stream == nullptr && out_host) {
     e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned timeouts = 0;
+    e = take_stage_timeouts(&timeouts, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stage timeouts");
+    if (timeouts) return fail(GNSS_ETIMEOUT, "a bounded wait of the staged correlate kernel gave up; results invalid");
   }
   return GNSS_OK;
 }
@@ -328,6 +332,7 @@ gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_dev, size_t
 gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint32_t n_blocks, float* surface_dev,
                                  gnss_detection* out_dev, void* stream) {
   if (!plan || !spectra_dev || !out_dev || n_blocks < 1) return fail(GNSS_EINVAL, "bad argument");
+  if ((uintptr_t)spectra_dev & 15u) return fail(GNSS_EINVAL, "spectra_dev must be 16-byte aligned");
   gnss_status st = check_plan_device(plan);
   if (st != GNSS_OK) return st;
   if ((plan->desc.flags & GNSS_SECOND_WHOLE) && !surface_dev)

@@ -465,10 +465,16 @@ __device__ __forceinline__ void pass_compute_tw(float2 (&v)[E], const FftTw<N, E
   }
 }
 
-// fft_block with the twiddle bases precomputed in 'tw' (see FftTw).
-template <int N, int E, bool INV, bool DOUBLE_BUF, int NS = 1>
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// fft_block with the twiddle bases precomputed in 'tw' (see FftTw).  'hook'
+// runs once, right after the first CTA barrier of the transform: by then
+// every thread has consumed the inputs it loaded before the transform.
+template <int N, int E, bool INV, bool DOUBLE_BUF, int NS = 1, typename Hook = NoHook>
 __device__ __forceinline__ void fft_block_tw(float2 (&v)[E], int j, float2* buf0, float2* buf1, int& phase,
-                                             const FftTw<N, E, INV, NS>& tw) {
+                                             const FftTw<N, E, INV, NS>& tw, const Hook& hook = Hook()) {
   constexpr int R = PassRadix<N, NS>::value;
   pass_compute_tw<N, E, R, NS, INV>(v, tw);
   if constexpr (NS * R < N) {
@@ -476,6 +482,7 @@ __device__ __forceinline__ void fft_block_tw(float2 (&v)[E], int j, float2* buf0
     if constexpr (!DOUBLE_BUF) __syncthreads();
     pass_store<N, E, R, NS>(v, j, buf);
     __syncthreads();
+    if constexpr (NS == 1) hook();
     gather_regs<N, E>(v, j, buf);
     if constexpr (DOUBLE_BUF) phase ^= 1;
     fft_block_tw<N, E, INV, DOUBLE_BUF, NS * R>(v, j, buf0, buf1, phase, tw.next);

@@ -124,7 +124,8 @@ bool supported_fft_size(int N);
 // Correlate-kernel variant (elements per thread E) per device and FFT size.
 int xcorr_variant(int N);
 int xcorr_default_e(int N);
-bool xcorr_valid_e(int N, int E);
+bool xcorr_valid_e(int N, int code);
+cudaError_t take_stage_timeouts(unsigned* count, cudaStream_t stream);
 void set_xcorr_variant(int N, int E);
 
 // Fine acquisition (refine.cu).

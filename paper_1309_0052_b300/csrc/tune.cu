@@ -2,7 +2,8 @@
 //
 // The correlate kernel (conj-multiply, IFFT, |.|^2, non-coherent sum) can
 // hold E = 16 or E = 32 FFT elements per thread: N / E threads per FFT,
-// different register budgets, occupancy and exchange costs.  Which one is
+// different register budgets, occupancy and exchange costs; with E = 16 it
+// can also stage the next block by a bulk TMA copy (more shared memory).  Which one is
 // faster depends on the FFT size (and the GPU), so gnss_autotune times every
 // valid choice on a probe shaped like the plan and records the fastest for
 // that FFT size on the current device; every later launch (single or
@@ -25,10 +26,11 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
   gnss_tune_result res;
   memset(&res, 0, sizeof(res));
   res.N = (uint32_t)N;
-  const int cand[2] = {16, 32};
+  const int cand[3] = {16, 32, 16 | (int)GNSS_TUNE_STAGED};
   if (force_elems) {
     if (!xcorr_valid_e(N, (int)force_elems))
-      return fail_status(GNSS_EINVAL, "elements per thread must be 16 (N <= 16384) or 32 (N >= 1024)");
+      return fail_status(GNSS_EINVAL, "variant must be 16 (N <= 16384), 32 (N >= 1024) or 16 | GNSS_TUNE_STAGED "
+                                      "(N <= 8192)");
     set_xcorr_variant(N, (int)force_elems);
     res.chosen = force_elems;
     if (out) *out = res;
@@ -65,7 +67,7 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
   const int prev = xcorr_variant(N);
   float best = 0.f;
   int best_e = prev;
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
     const int E = cand[k];
     if (!xcorr_valid_e(N, E)) continue;
     set_xcorr_variant(N, E);
