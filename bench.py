@@ -168,6 +168,8 @@ def make_workloads(args):
     import multiprocessing as mp
     rec = siggen.weak_100ms()
     long_rec = None if args.no_code_doppler else siggen.long_400ms()
+    ref_rec = None if args.no_refine else siggen.refine_12ms()
+    trk_rec = None if args.no_track else siggen.track_1s()
     batch, serve = [], []
     if not args.no_batch or not args.no_serve:
         n = os.cpu_count() or 1
@@ -183,7 +185,7 @@ def make_workloads(args):
                 batch = [by_idx[i] for i in range(args.batch_requests)]
             if not args.no_serve:
                 serve = siggen.serving_requests(args.serve_pool)
-    return rec, batch, serve, long_rec
+    return rec, batch, serve, long_rec, ref_rec, trk_rec
 
 
 def run_batch(g, torch, batch, stream, flush, steps):
@@ -264,6 +266,104 @@ def run_code_doppler(g, torch, rec, stream, flush, steps):
         res[name] = {"ms_per_request": t, "cells_per_s": cells / (t * 1e-3),
                      "detected_prns": sorted(int(d["prn"]) for d in det if d["detected"])}
     return res
+
+
+def run_refine(g, torch, rec, stream, steps):
+    """Fine acquisition of the 12 ms recording: the detections of a plain
+    acquisition (true candidates) plus 1000 seeded random candidates, refined
+    over 10 ms on the device (Doppler pre-search +-250 Hz, then gradient
+    ascent); time per call and the refined error of the true candidates
+    against the injected truth (delay at the middle of the window)."""
+    coh = 10
+    plan = g.Plan.for_recording(rec)
+    raw = torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda()
+    det = plan.acquire(raw, rec.n_samples)
+    true = [(int(d["prn"]), float(d["dopp_hz"]), int(d["code_phase"]) * 1023.0 / plan.N) for d in det if d["detected"]]
+    rprn, rf, rtau = siggen.refine_candidates(rec)
+    prn = [t[0] for t in true] + list(rprn)
+    cands = g.candidates(prn, [t[1] for t in true] + list(rf), [t[2] for t in true] + list(rtau))
+    cands_dev = torch.from_numpy(cands.view(np.uint8)).cuda()
+    out_dev = torch.zeros(len(cands) * g.REFINED_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+
+    def call():
+        plan.refine_device(raw, rec.n_samples, cands_dev, len(cands), coh, 100, out_dev, search_hz=250.0,
+                           stream=stream)
+
+    with torch.cuda.stream(stream):
+        call()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            call()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    out = np.frombuffer(out_dev.cpu().numpy().tobytes(), g.REFINED_DTYPE)
+    T = coh * plan.N / rec.fs
+    truth = {s.prn: s for s in rec.sats}
+    df, dt = [], []
+    for k, (p, _, _) in enumerate(true):
+        s = truth.get(p)
+        if s is None:
+            continue
+        df.append(out[k]["f_hz"] - s.dopp_hz)
+        mid = s.code_phase_chips - s.dopp_hz * T / (2 * 1540.0)
+        dt.append((out[k]["tau_chips"] - mid + 511.5) % 1023 - 511.5)
+    t = statistics.median(ms)
+    return {"workload": "refine_12ms: 2.048 MHz int8, %d true + %d random candidates, 10 ms window, "
+                        "pre-search +-250 Hz, <= 100 iterations" % (len(true), len(rprn)),
+            "ms_per_call": t, "candidates_per_s": len(cands) / (t * 1e-3),
+            "true_candidates": len(df),
+            "rms_doppler_error_hz": float(np.sqrt(np.mean(np.square(df)))) if df else None,
+            "rms_delay_error_chips": float(np.sqrt(np.mean(np.square(dt)))) if dt else None,
+            "status_counts": {int(k): int(v) for k, v in zip(*np.unique(out["status"], return_counts=True))}}
+
+
+def run_track(g, torch, rec, stream, steps, n_chan=1280):
+    """Tracking channels over the 1 s recording: the 8 injected satellites
+    from perturbed truth plus seeded channels on every PRN at random (f, tau)
+    up to n_chan, 1000 intervals of 1 ms each, one launch; channel-ms per
+    second and the lock of the true channels."""
+    plan = g.Plan.for_recording(rec)
+    raw = torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda()
+    prn, f, tau = siggen.track_starts(rec)
+    rng = np.random.default_rng(1309005207)
+    extra = n_chan - len(prn)
+    prn = np.concatenate([prn, 1 + np.arange(extra) % 32])
+    f = np.concatenate([f, rng.uniform(-5000.0, 5000.0, extra)])
+    tau = np.concatenate([tau, rng.uniform(0.0, 1023.0, extra)])
+    cands = g.candidates(prn, f, tau)
+    cdev = torch.from_numpy(cands.view(np.uint8)).cuda()
+    n_int = rec.n_samples // plan.N
+    out = torch.zeros(len(cands) * n_int * g.TRACK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+
+    def call():
+        plan.track(raw, rec.n_samples, cdev, len(cands), out, n_int, 1, 1.0, 15.0, 2.0, stream=stream)
+
+    with torch.cuda.stream(stream):
+        call()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            call()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    recs = g.track_records(out[: len(rec.sats) * n_int * g.TRACK_DTYPE.itemsize].cpu().numpy())
+    recs = recs.reshape(len(rec.sats), n_int)[:, -200:]
+    lock = [float(np.mean(r["zp"][:, 1] ** 2) / max(np.mean(r["zp"][:, 0] ** 2), 1e-30)) for r in recs]
+    t = statistics.median(ms)
+    return {"workload": "track_1s: 4.096 MHz 2-bit, 1 s, %d channels (8 injected satellites + seeded channels "
+                        "on every PRN), 1000 intervals of 1 ms, E/P/L spacing 1 chip, PLL 15 Hz, DLL 2 Hz" % n_chan,
+            "ms_per_launch": t, "channel_ms_per_s": len(cands) * n_int / (t * 1e-3),
+            "sample_correlations_per_s": 3 * len(cands) * rec.n_samples / (t * 1e-3),
+            "true_channels_q2_over_i2_last_200ms": lock}
 
 
 def run_serving(g, serve, rate, seconds, seed=1309005205):
@@ -407,7 +507,7 @@ def _dist():
 
 
 def run_ours(args):
-    rec, batch, serve, long_rec = make_workloads(args)
+    rec, batch, serve, long_rec, ref_rec, trk_rec = make_workloads(args)
     import torch
     import paper_1309_0052_b300 as g
 
@@ -516,6 +616,10 @@ def run_ours(args):
                                                         steps=10, ours_ms=x_ms)
     if long_rec is not None:
         line["code_doppler"] = run_code_doppler(g, torch, long_rec, stream, flush, steps=10)
+    if ref_rec is not None:
+        line["refine"] = run_refine(g, torch, ref_rec, stream, steps=10)
+    if trk_rec is not None:
+        line["track"] = run_track(g, torch, trk_rec, stream, steps=3)
     if batch:
         line["batch"] = run_batch(g, torch, batch, stream, flush, steps=3)
     if serve:
@@ -623,6 +727,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-code-doppler", action="store_true")
+    ap.add_argument("--no-refine", action="store_true")
+    ap.add_argument("--no-track", action="store_true")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-rates", default="50,100,200",
                     help="offered Poisson arrival rates (requests/s), one serving run each")

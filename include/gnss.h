@@ -345,6 +345,65 @@ GNSS_API gnss_status gnss_refine_device(gnss_plan* plan, const void* samples_dev
                                         uint32_t max_iter, double search_hz, gnss_refined* out_dev, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Tracking channels (Section 3, Fig. 3).  A tracking channel shares the
+ * carrier and code NCOs and the first mixing stage with acquisition, but
+ * correlates in the time domain at early / prompt / late code offsets and
+ * closes a carrier loop and a code loop around them.  The paper gives the
+ * channel as a block diagram; the loop design here is this library's
+ * reading, built like a hardware receiver's:
+ *   NCOs in fixed point: carrier phase Phi (uint32, 2^32 = one cycle), word
+ *     Wc = round(f 2^32 / fs) (two's complement); code position P in units of
+ *     2^-32 chip in [0, 1023 2^32), word Wk = round(f_code 2^32 / fs)
+ *     (rounding half away from zero).
+ *   Interval k = samples kL + i, i < L = coh_ms N:
+ *     s_i   = x[kL + i] exp(-j 2 pi (Phi + i Wc) / 2^32),
+ *     Z_E/P/L = sum s_i c[floor((P + i Wk + {+h, 0, -h}) / 2^32) mod 1023],
+ *     h = round(spacing / 2 * 2^32); the record's delay is (-P / 2^32) mod 1023
+ *     chips at the interval start; then Phi += L Wc, P += L Wk.
+ *   e_phi = atan(Q_P / I_P) / (2 pi) cycles (Costas; 0 when Z_P = 0),
+ *   e_tau = (1 - spacing / 2) (|Z_L| - |Z_E|) / (|Z_L| + |Z_E|) chips.
+ *   PLL, 2nd order, zeta = 1/sqrt(2), w_n = 8 zeta B_pll / (4 zeta^2 + 1):
+ *     f_int += w_n^2 T e_phi,  f = f_int + 2 zeta w_n e_phi  (T = L / fs).
+ *   DLL, 1st order, carrier aided: f_code = R_c (1 + f / f_L1) - 4 B_dll e_tau,
+ *     f_L1 = 1540 R_c.
+ *   Start: f_int = f = f0 (channel f_hz), Phi = 0, P = round(-tau0 2^32) mod.
+ * Correlator sums in FP32, loop state in double.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t coh_ms;       /* integration interval (ms), 1..1000                     */
+  uint32_t n_int;        /* intervals to run from the recording start, >= 1         */
+  float spacing_chips;   /* early-late spacing in (0, 1]                            */
+  float pll_bw_hz;       /* PLL noise bandwidth, 0..1000 (0 = carrier NCO free-runs) */
+  float dll_bw_hz;       /* DLL noise bandwidth, 0..1000 (0 = carrier aiding only)   */
+  uint32_t reserved;
+} gnss_track_config;
+
+typedef struct {
+  double f_hz;          /* carrier NCO frequency of the interval (Hz), Wc fs / 2^32 */
+  double tau_chips;     /* replica code delay at the interval start, [0, 1023)     */
+  float ze[2];          /* early correlator (I, Q)                                  */
+  float zp[2];          /* prompt correlator                                       */
+  float zl[2];          /* late correlator                                         */
+  float e_phi;          /* Costas discriminator (cycles)                            */
+  float e_tau;          /* DLL discriminator (chips)                                */
+  int32_t status;       /* 0; -1 PRN not in the plan; -2 an NCO left its range     */
+                        /* (the channel stops and its later records say -2)        */
+  uint32_t reserved;
+} gnss_track_rec;       /* 56 bytes */
+
+/* Track n_chan channels over one recording: channel c starts from
+ * chans_dev[c] (PRN, f_hz, tau_chips: e.g. refined acquisition results) and
+ * writes out_dev[c * n_int + k] for intervals k < n_int.  The plan supplies
+ * fs (N >= 2048: under one chip per sample), the recording format and the
+ * PRN codes.  samples_dev, chans_dev and out_dev are device pointers; the
+ * work is enqueued on 'stream' (one CTA per channel).  Errors: GNSS_EINVAL
+ * (NULL arguments, fs < 2.048 MHz, configuration out of range, n_int * L >
+ * n_samples, misaligned samples), GNSS_ECUDA. */
+GNSS_API gnss_status gnss_track(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                const gnss_candidate* chans_dev, size_t n_chan, const gnss_track_config* cfg,
+                                gnss_track_rec* out_dev, void* stream);
+
+/* ------------------------------------------------------------------------
  * Serving.  The paper's cloud deployment runs many receiver instances per
  * server and rates throughput by the effective running time of concurrent
  * instances (Section 4); for the GPU it names fewer, larger operations as the

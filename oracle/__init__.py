@@ -65,6 +65,8 @@ def _L():
         _lib.orc_detect.argtypes = [P, i, i, i, i, i, i, d, P, P]
         _lib.orc_refine_eval.argtypes = [P, P, i64, d, P, d, d, P, P]
         _lib.orc_refine.argtypes = [P, P, i64, d, P, d, d, i, d, P]
+        _lib.orc_track.argtypes = [P, P, i64, i64, i, i, P, d, d, d, d, d, P]
+        _lib.orc_track.restype = i
     return _lib
 
 
@@ -252,3 +254,22 @@ def refine(x, L: int, fs: float, chips, f0: float, tau0: float, max_iter: int = 
     _L().orc_refine(_p(xr), _p(xi), int(L), float(fs), _p(chips), float(f0), float(tau0),
                     int(max_iter), float(search_hz), C.byref(r))
     return dict(f=r.f, tau=r.tau, P=r.P, iters=r.iters, status=r.status)
+
+
+TRACK_DTYPE = np.dtype([("f_hz", "<f8"), ("tau_chips", "<f8"), ("ze", "<f8", (2,)), ("zp", "<f8", (2,)),
+                        ("zl", "<f8", (2,)), ("e_phi", "<f8"), ("e_tau", "<f8")])
+
+
+def track(x, fs: int, coh_ms: int, n_int: int, chips, f0: float, tau0: float, spacing: float = 1.0,
+          b_pll: float = 15.0, b_dll: float = 1.0) -> np.ndarray:
+    """Tracking channel over n_int intervals of coh_ms ms from the recording
+    start: per interval the NCO frequency, the replica delay at its start,
+    the early / prompt / late correlators and both discriminators."""
+    xr, xi = _split(x)
+    chips = np.ascontiguousarray(chips, np.int8)
+    out = np.zeros(n_int, TRACK_DTYPE)
+    rc = _L().orc_track(_p(xr), _p(xi), len(xr), int(fs), int(coh_ms), int(n_int), _p(chips), float(f0),
+                        float(tau0), float(spacing), float(b_pll), float(b_dll), _p(out))
+    if rc != 0:
+        raise ValueError("bad tracking arguments (%d)" % rc)
+    return out

@@ -17,7 +17,9 @@
  *   - power surfaces (optionally code-Doppler compensated), peak /
  *     second-peak detection, and
  *   - the coherent-power objective of fine acquisition, its analytic
- *     gradient and a gradient-ascent refinement.
+ *     gradient and a gradient-ascent refinement, and
+ *   - a tracking channel: fixed-point carrier and code NCOs, early / prompt /
+ *     late correlators, Costas PLL and carrier-aided DLL.
  *
  * The paper describes the acquisition channel only at block-diagram level:
  * code NCO -> replica, carrier NCO -> first mixing, FFT of the mixed signal
@@ -672,4 +674,114 @@ void orc_refine(const double *xr, const double *xi, int64_t L, double fs,
   out->P = P;
   out->iters = it;
   out->status = status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tracking channel (Section 3, Fig. 3): carrier and code NCOs, the first    */
+/* mixing stage and time-domain early / prompt / late correlation, closed by */
+/* a Costas phase-locked loop and a carrier-aided delay-locked loop.         */
+/* ------------------------------------------------------------------------ */
+
+/* The paper gives the tracking channel as a block diagram only; the loop
+ * design below is this library's reading, written the way a hardware
+ * receiver builds it.
+ *
+ * NCOs (fixed point, exact integer arithmetic):
+ *   carrier phase  Phi (uint32, 2^32 = one cycle), word Wc = round(f 2^32 / fs)
+ *                  as a two's-complement 32-bit increment per sample;
+ *   code position  P (units of 2^-32 chip, kept in [0, 1023 2^32)), word
+ *                  Wk = round(f_code 2^32 / fs) per sample (needs f_code < fs).
+ * Interval k covers samples n = k L + i, i < L (L = coh_ms N):
+ *   theta_i = Phi + i Wc (mod 2^32),   u_i = P + i Wk,
+ *   s_i     = x[n] exp(-j 2 pi theta_i / 2^32),
+ *   Z_E     = sum s_i c[floor((u_i + h) / 2^32) mod 1023],
+ *   Z_P     = sum s_i c[floor(u_i / 2^32) mod 1023],
+ *   Z_L     = sum s_i c[floor((u_i - h) / 2^32) mod 1023],
+ * with h = round(spacing / 2 * 2^32) (early and late replicas half the
+ * early-late spacing ahead of and behind the prompt one).  The replica delay
+ * at the interval start is tau_k = (-P / 2^32) mod 1023 chips (k L samples
+ * span a whole number of code periods).  Then Phi += L Wc, P += L Wk (mod).
+ * Discriminators:
+ *   e_phi = atan(Q_P / I_P) / (2 pi) cycles (Costas: blind to data bits;
+ *           0 when Z_P = 0),
+ *   e_tau = (1 - spacing / 2) (|Z_L| - |Z_E|) / (|Z_L| + |Z_E|) chips (the
+ *           delay error of a triangular correlation peak within half the
+ *           spacing; 0 when both are 0).
+ * Loops (T = L / fs):
+ *   PLL, second order, noise bandwidth B_pll, zeta = 1/sqrt(2),
+ *       w_n = 8 zeta B_pll / (4 zeta^2 + 1):
+ *       f_int += w_n^2 T e_phi,   f = f_int + 2 zeta w_n e_phi   (Hz);
+ *   DLL, first order with carrier aiding, noise bandwidth B_dll:
+ *       f_code = R_c (1 + f / f_L1) - 4 B_dll e_tau   (chip/s),
+ *       f_L1 = 1540 R_c (the code Doppler is the carrier Doppler / 1540).
+ * Start: f_int = f = f0, Phi = 0, P = round(-tau0 2^32) mod (1023 2^32). */
+typedef struct {
+  double f_hz;      /* carrier NCO frequency of the interval, Wc fs / 2^32 */
+  double tau_chips; /* replica delay at the interval start */
+  double ze[2], zp[2], zl[2];
+  double e_phi, e_tau;
+} orc_track_rec;
+
+static uint32_t orc_round_word(double v) { /* round half away, to 32 bits */
+  return (uint32_t)(int64_t)llround(v);
+}
+
+int orc_track(const double *xr, const double *xi, int64_t n_samples, int64_t fs, int coh_ms,
+              int n_int, const int8_t *chips, double f0, double tau0, double spacing,
+              double b_pll, double b_dll, orc_track_rec *out) {
+  const int64_t N = fs / 1000, L = (int64_t)coh_ms * N;
+  const double two32 = 4294967296.0;
+  const int64_t period = (int64_t)ORC_CHIPS << 32;
+  if (fs % 1000 || (int64_t)n_int * L > n_samples || spacing <= 0.0 || spacing > 1.0) return -1;
+  const double T = (double)L / (double)fs;
+  const double zeta = 1.0 / sqrt(2.0);
+  const double wn = 8.0 * zeta * b_pll / (4.0 * zeta * zeta + 1.0);
+  const double f_l1 = 1540.0 * ORC_CHIP_RATE;
+  const uint32_t h = orc_round_word(spacing * 0.5 * two32);
+  double f_int = f0, f = f0, e_tau = 0.0;
+  uint32_t phi = 0;
+  int64_t P = llround(-tau0 * two32) % period;
+  if (P < 0) P += period;
+  for (int k = 0; k < n_int; ++k) {
+    const double f_code = ORC_CHIP_RATE * (1.0 + f / f_l1) - 4.0 * b_dll * e_tau;
+    if (f_code <= 0.0 || f_code >= (double)fs || fabs(f) >= 0.5 * (double)fs) return -2;
+    const uint32_t wc = orc_round_word(f * two32 / (double)fs);
+    const uint32_t wk = orc_round_word(f_code * two32 / (double)fs);
+    double z[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int64_t i = 0; i < L; ++i) {
+      const int64_t n = (int64_t)k * L + i;
+      const uint32_t theta = phi + (uint32_t)i * wc;
+      const double ang = 2.0 * ORC_PI * (double)theta / two32;
+      const double c = cos(ang), s = -sin(ang);
+      const double sr = xr[n] * c - xi[n] * s, si = xr[n] * s + xi[n] * c;
+      const int64_t u = P + i * (int64_t)wk; /* below (coh + 2) periods: no overflow */
+      const int64_t pos[3] = {u + (int64_t)h, u, u - (int64_t)h};
+      for (int r = 0; r < 3; ++r) {
+        /* pos >= -2^31: one period added keeps it positive, so the division
+         * by 2^32 is a floor */
+        const int64_t chip = ((pos[r] + period) / ((int64_t)1 << 32)) % ORC_CHIPS;
+        z[r][0] += sr * chips[chip];
+        z[r][1] += si * chips[chip];
+      }
+    }
+    orc_track_rec *o = out + k;
+    o->f_hz = (double)(int32_t)wc * (double)fs / two32;
+    o->tau_chips = (double)((period - P) % period) / two32;
+    for (int r = 0; r < 2; ++r) {
+      o->ze[r] = z[0][r];
+      o->zp[r] = z[1][r];
+      o->zl[r] = z[2][r];
+    }
+    const double ip = z[1][0], qp = z[1][1];
+    const double e_phi = (ip == 0.0 && qp == 0.0) ? 0.0 : atan(qp / ip) / (2.0 * ORC_PI);
+    const double me = hypot(z[0][0], z[0][1]), ml = hypot(z[2][0], z[2][1]);
+    e_tau = (me + ml > 0.0) ? (1.0 - spacing / 2.0) * (ml - me) / (ml + me) : 0.0;
+    o->e_phi = e_phi;
+    o->e_tau = e_tau;
+    phi += (uint32_t)L * wc;
+    P = (P + L * (int64_t)wk) % period;
+    f_int += wn * wn * T * e_phi;
+    f = f_int + 2.0 * zeta * wn * e_phi;
+  }
+  return 0;
 }

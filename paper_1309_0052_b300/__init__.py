@@ -64,6 +64,17 @@ REFINED_DTYPE = np.dtype([("f_hz", "<f8"), ("tau_chips", "<f8"), ("power", "<f4"
                           ("status", "<i4"), ("reserved", "<u4")])
 assert CANDIDATE_DTYPE.itemsize == 24 and REFINED_DTYPE.itemsize == 32
 
+TRACK_DTYPE = np.dtype([("f_hz", "<f8"), ("tau_chips", "<f8"), ("ze", "<f4", (2,)), ("zp", "<f4", (2,)),
+                        ("zl", "<f4", (2,)), ("e_phi", "<f4"), ("e_tau", "<f4"), ("status", "<i4"),
+                        ("reserved", "<u4")])
+assert TRACK_DTYPE.itemsize == 56
+
+
+class TrackConfig(C.Structure):
+    _fields_ = [("coh_ms", C.c_uint32), ("n_int", C.c_uint32), ("spacing_chips", C.c_float),
+                ("pll_bw_hz", C.c_float), ("dll_bw_hz", C.c_float), ("reserved", C.c_uint32)]
+
+
 DETECTION_DTYPE = np.dtype([("prn", "u1"), ("detected", "u1"), ("set", "u1"), ("reserved", "u1"),
                             ("dopp_bin", "<i4"), ("dopp_hz", "<i4"), ("code_phase", "<u4"),
                             ("peak", "<f4"), ("second", "<f4"), ("ratio", "<f4")])
@@ -88,6 +99,7 @@ _SIGS = {
                     _st),
     "gnss_refine_device": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_double, _P, _P], _st),
     "gnss_acquire_batch": ([_P, C.c_size_t, C.c_size_t, _P], _st),
+    "gnss_track": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.POINTER(TrackConfig), _P, _P], _st),
     "gnss_server_create": ([_P, C.POINTER(_P)], _st),
     "gnss_server_destroy": ([_P], _st),
     "gnss_submit": ([_P, C.POINTER(PlanDesc), _P, C.c_size_t, C.POINTER(C.c_uint64)], _st),
@@ -286,6 +298,14 @@ class Plan:
                                       _ptr(tau_dev), prn_dev.numel(), _ptr(P_dev), _ptr(dPdf_dev),
                                       _ptr(dPdtau_dev), _stream_ptr(stream)), "gnss_refine_eval")
 
+    def track(self, samples_dev, n_samples: int, chans_dev, n_chan: int, out_dev, n_int: int, coh_ms: int = 1,
+              spacing: float = 1.0, pll_bw_hz: float = 15.0, dll_bw_hz: float = 1.0, stream=None) -> None:
+        """gnss_track on CUDA tensors: chans_dev holds n_chan candidate
+        records (candidates()), out_dev n_chan * n_int track records."""
+        cfg = TrackConfig(coh_ms, n_int, spacing, pll_bw_hz, dll_bw_hz, 0)
+        check(load().gnss_track(self._h, _ptr(samples_dev), n_samples, _ptr(chans_dev), n_chan, C.byref(cfg),
+                                _ptr(out_dev), _stream_ptr(stream)), "gnss_track")
+
     def stage_correlate(self, spectra_dev, n_blocks: int, out_dev, surface=None, stream=None) -> None:
         check(load().gnss_stage_correlate(self._h, _ptr(spectra_dev), n_blocks, _ptr(surface), _ptr(out_dev),
                                        _stream_ptr(stream)), "gnss_stage_correlate")
@@ -383,3 +403,8 @@ def probe_ffma(iters: int = 4096, stream=None):
 def detections_from_bytes(buf) -> np.ndarray:
     """View a device-side detection buffer copied to host (uint8) as records."""
     return np.frombuffer(np.asarray(buf, np.uint8).tobytes(), DETECTION_DTYPE)
+
+
+def track_records(buf) -> np.ndarray:
+    """Track records from the raw bytes of a device output buffer."""
+    return np.frombuffer(np.asarray(buf).tobytes(), TRACK_DTYPE)

@@ -279,6 +279,25 @@ def long_400ms(seed: int = SEED_BASE + 6) -> Recording:
                           half_bit=True)
 
 
+def track_1s(seed: int = SEED_BASE + 7) -> Recording:
+    """Tracking recording: fs 4.096 MHz, 1 s 2-bit packed I/Q (2,048,000
+    bytes), 8 satellites at C/N0 38-48 dB-Hz, Doppler in +-4.5 kHz, Doppler
+    rate 0.5 Hz/s, data bits every 20 ms."""
+    return make_recording(seed, 4_096_000, 4_096_000, FMT_2BIT_IQ, 8, (38.0, 48.0), (-4500.0, 4500.0),
+                          rate=0.5, coh_ms=1, dopp_min_hz=-5000, dopp_step_hz=500, n_dopp=21)
+
+
+def track_starts(rec: Recording, seed: int = SEED_BASE + 7):
+    """Tracking start points of the injected satellites, as a refined
+    acquisition would hand them over: truth Doppler + U(-5, 5) Hz, truth code
+    phase + U(-0.1, 0.1) chip.  Returns (prn, f Hz, tau chips) arrays."""
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    prn = np.array([s.prn for s in rec.sats])
+    f = np.array([s.dopp_hz for s in rec.sats]) + rng.uniform(-5.0, 5.0, len(prn))
+    tau = (np.array([s.code_phase_chips for s in rec.sats]) + rng.uniform(-0.1, 0.1, len(prn))) % CHIPS
+    return prn, f, tau
+
+
 def serving_requests(n_req: int, seed: int = SEED_BASE + 5, ms_range=(10, 500),
                      fs_choices=(2_048_000, 4_096_000, 8_192_000, 16_384_000)) -> list:
     """Serving workload: recordings 10-500 ms, fs in {2.048 .. 16.384} MHz,

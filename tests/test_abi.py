@@ -105,6 +105,8 @@ def test_host_side_rejections_of_later_entry_points(lib):
     fn = L.gnss_acquire_noalloc
     fn.argtypes = [C.c_void_p] * 3 + [C.c_void_p] * 3
     assert fn(None, None, 0, None, None, None) == E
+    cfg = lib.TrackConfig(1, 10, 1.0, 15.0, 1.0, 0)
+    assert L.gnss_track(None, None, 0, None, 1, C.byref(cfg), None, None) == E
 
 
 def test_record_layouts_match_the_header(lib, tmp_path):
@@ -117,11 +119,13 @@ def test_record_layouts_match_the_header(lib, tmp_path):
 #include <stdio.h>
 #include "gnss.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gnss_plan_desc), sizeof(gnss_detection),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gnss_plan_desc), sizeof(gnss_detection),
          sizeof(gnss_candidate), sizeof(gnss_refined), sizeof(gnss_request), sizeof(gnss_server_config),
-         sizeof(gnss_server_stats), sizeof(gnss_tune_result), sizeof(gnss_plan_info));
-  printf("%zu %zu %zu %zu\n", offsetof(gnss_detection, dopp_bin), offsetof(gnss_detection, ratio),
-         offsetof(gnss_refined, status), offsetof(gnss_plan_desc, prn_mask));
+         sizeof(gnss_server_stats), sizeof(gnss_tune_result), sizeof(gnss_plan_info), sizeof(gnss_track_config),
+         sizeof(gnss_track_rec));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(gnss_detection, dopp_bin), offsetof(gnss_detection, ratio),
+         offsetof(gnss_refined, status), offsetof(gnss_plan_desc, prn_mask), offsetof(gnss_track_rec, zl),
+         offsetof(gnss_track_rec, status));
   return 0;
 }
 """)
@@ -130,6 +134,8 @@ int main(void) {
     sizes, offs = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().splitlines()]
     assert sizes == [C.sizeof(lib.PlanDesc), lib.DETECTION_DTYPE.itemsize, lib.CANDIDATE_DTYPE.itemsize,
                      lib.REFINED_DTYPE.itemsize, C.sizeof(lib.Request), C.sizeof(lib.ServerConfig),
-                     C.sizeof(lib.ServerStats), C.sizeof(lib.TuneResult), C.sizeof(lib.PlanInfo)]
+                     C.sizeof(lib.ServerStats), C.sizeof(lib.TuneResult), C.sizeof(lib.PlanInfo),
+                     C.sizeof(lib.TrackConfig), lib.TRACK_DTYPE.itemsize]
     assert offs == [lib.DETECTION_DTYPE.fields["dopp_bin"][1], lib.DETECTION_DTYPE.fields["ratio"][1],
-                    lib.REFINED_DTYPE.fields["status"][1], lib.PlanDesc.prn_mask.offset]
+                    lib.REFINED_DTYPE.fields["status"][1], lib.PlanDesc.prn_mask.offset,
+                    lib.TRACK_DTYPE.fields["zl"][1], lib.TRACK_DTYPE.fields["status"][1]]
