@@ -20,15 +20,18 @@
 //   DLL, carrier aided: e_tau = (1 - spacing/2) (|Z_L| - |Z_E|) / (|Z_L| + |Z_E|),
 //     f_code = R_c (1 + f / f_L1) - 4 B_dll e_tau, f_L1 = 1540 R_c.
 //
-// One CTA per channel runs the intervals in order.  Each thread takes a
-// contiguous run of L / 256 samples in groups of 8: the carrier is started
+// A group of threads per channel -- the whole CTA when there are few
+// channels, one warp when there are enough to fill the GPU -- runs the
+// intervals in order.  Each thread takes a contiguous run of the interval's
+// samples in groups of 8: the carrier is started
 // from its exact NCO phase for every group (sincospif of the 32-bit phase)
 // and rotated by one sample's phase inside it; the code NCO runs in 64-bit
 // integers and the three replica chips are read from a 32-chip window of a
 // bit table of the PRN's code in shared memory (bit = 1 for chip -1), so the
-// +-1 multiplies are sign flips.  Sums are FP32, reduced over the CTA; the
-// loop update (discriminators and filters) runs in double on thread 0 and
-// hands the next interval's NCO words to the CTA through shared memory.
+// +-1 multiplies are sign flips.  Sums are FP32, reduced over the group; the
+// group's first thread forms the discriminators (FP32), runs the loop filters
+// in double and hands the next interval's NCO words to the group through
+// shared memory.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -112,19 +115,32 @@ __device__ __forceinline__ float flip(float v, uint32_t sign_bit) {
   return __int_as_float(__float_as_int(v) ^ (int)sign_bit);
 }
 
-template <int FMT>
+// Barrier of one channel's thread group: a warp, or the whole CTA.
+template <int TPC>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (TPC == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// TPC threads per channel (32: one warp per channel, 256 / 32 channels per
+// CTA; 256: one CTA per channel).
+template <int FMT, int TPC>
 __global__ void __launch_bounds__(kTrackThreads) k_track(const TrackJob J, const gnss_candidate* __restrict__ chans,
-                                                         gnss_track_rec* __restrict__ out) {
-  constexpr int T = kTrackThreads, W = T / 32;
-  __shared__ uint32_t s_code[kCodeWords];
-  __shared__ float s_red[6][W];
-  __shared__ TrackNco s_nco;
-  const int t = threadIdx.x;
-  const gnss_candidate ch = chans[blockIdx.x];
+                                                         int n_chan, gnss_track_rec* __restrict__ out) {
+  constexpr int CPC = kTrackThreads / TPC;  // channels per CTA
+  constexpr int W = TPC / 32;               // warps per channel
+  __shared__ uint32_t s_code[CPC][kCodeWords];
+  __shared__ float s_red[CPC][6][W];
+  __shared__ TrackNco s_nco[CPC];
+  const int lc = threadIdx.x / TPC;
+  const int t = threadIdx.x % TPC;
+  const int c = blockIdx.x * CPC + lc;
+  if (c >= n_chan) return;  // whole warps only (TPC = 32 when CPC > 1)
+  const gnss_candidate ch = chans[c];
   const int row = (ch.prn >= 1 && ch.prn <= 32) ? __ldg(J.prn_index + ch.prn) : -1;
-  gnss_track_rec* rec = out + (size_t)blockIdx.x * J.n_int;
+  gnss_track_rec* rec = out + (size_t)c * J.n_int;
   if (row < 0) {  // PRN not in the plan: every record says so
-    for (int k = t; k < J.n_int; k += T) {
+    for (int k = t; k < J.n_int; k += TPC) {
       gnss_track_rec r = {};
       r.status = -1;
       rec[k] = r;
@@ -132,7 +148,8 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(const TrackJob J, const
     return;
   }
   const int8_t* code = J.codes + (size_t)row * 1023;
-  for (int w = t; w < kCodeWords; w += T) {
+  uint32_t* tab = s_code[lc];
+  for (int w = t; w < kCodeWords; w += TPC) {
     uint32_t v = 0;
     for (int b = 0; b < 32; ++b) {
       const int bit = 32 * w + b;
@@ -141,25 +158,26 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(const TrackJob J, const
         if (code[chip] < 0) v |= 1u << b;
       }
     }
-    s_code[w] = v;
+    tab[w] = v;
   }
-  // thread 0 owns the loop state
+  // the group's first thread owns the loop state
   const double two32 = 4294967296.0;
   const int64_t period = (int64_t)1023 << 32;
-  double f_int = ch.f_hz, f = ch.f_hz, e_tau = 0.0;
+  double f_int = ch.f_hz, f = ch.f_hz;
+  TrackNco& nco_s = s_nco[lc];
   if (t == 0) {
     int64_t P = llround(-ch.tau_chips * two32) % period;
     if (P < 0) P += period;
-    s_nco.P = P;
-    s_nco.phi = 0;
-    s_nco.status = track_words(J, f, 0.0, &s_nco.wc, &s_nco.wk);
+    nco_s.P = P;
+    nco_s.phi = 0;
+    nco_s.status = track_words(J, f, 0.0, &nco_s.wc, &nco_s.wk);
   }
-  __syncthreads();
-  const int S = J.L / T;  // samples per thread, a multiple of 8
+  group_sync<TPC>();
+  const int S = J.L / TPC;  // samples per thread, a multiple of 8
   const int i0 = t * S;
   for (int k = 0; k < J.n_int; ++k) {
-    const TrackNco nco = s_nco;
-    if (nco.status != 0) {  // uniform: every thread read the same word
+    const TrackNco nco = nco_s;
+    if (nco.status != 0) {  // uniform over the group: every thread read the same word
       if (t == 0)
         for (int kk = k; kk < J.n_int; ++kk) {
           gnss_track_rec r = {};
@@ -177,10 +195,10 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(const TrackJob J, const
       track_load8<FMT>(J.samples, nk + i, xi, xq);
       float2 car = nco_carrier(nco.phi + (uint32_t)i * nco.wc);
       const int64_t u0 = nco.P + (int64_t)i * nco.wk;
-      const int kc = (int)((u0 >> 32) % 1023);             // chip of the group's first sample
-      const uint32_t frac = (uint32_t)u0;
-      const uint32_t win = __funnelshift_r(s_code[kc >> 5], s_code[(kc >> 5) + 1], kc & 31);  // chips kc-1 ..
-      uint64_t acc = frac;
+      const uint32_t chip0 = (uint32_t)(u0 >> 32);  // < 1023 (coh + 2)
+      const int kc = (int)(chip0 % 1023u);           // chip of the group's first sample
+      const uint32_t win = __funnelshift_r(tab[kc >> 5], tab[(kc >> 5) + 1], kc & 31);  // chips kc - 1 ..
+      uint64_t acc = (uint32_t)u0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const float sr = xi[e] * car.x - xq[e] * car.y;
@@ -201,49 +219,54 @@ __global__ void __launch_bounds__(kTrackThreads) k_track(const TrackJob J, const
         acc += nco.wk;
       }
     }
-    // CTA sums of the six correlator components
+    // group sums of the six correlator components
     float v[6] = {ze_r, ze_i, zp_r, zp_i, zl_r, zl_i};
 #pragma unroll
     for (int q = 0; q < 6; ++q)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    if ((t & 31) == 0)
+    if constexpr (W > 1) {
+      if ((t & 31) == 0)
 #pragma unroll
-      for (int q = 0; q < 6; ++q) s_red[q][t >> 5] = v[q];
-    __syncthreads();
+        for (int q = 0; q < 6; ++q) s_red[lc][q][t >> 5] = v[q];
+      group_sync<TPC>();
+      if (t == 0)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          float a = 0.f;
+          for (int w = 0; w < W; ++w) a += s_red[lc][q][w];
+          v[q] = a;
+        }
+    }
     if (t == 0) {
-      double z[6];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        double a = 0.0;
-        for (int w = 0; w < W; ++w) a += (double)s_red[q][w];
-        z[q] = a;
-      }
-      const double ip = z[2], qp = z[3];
-      const double e_phi = (ip == 0.0 && qp == 0.0) ? 0.0 : atan(qp / ip) / (2.0 * 3.14159265358979323846);
-      const double me = hypot(z[0], z[1]), ml = hypot(z[4], z[5]);
-      e_tau = (me + ml > 0.0) ? (1.0 - J.spacing / 2.0) * (ml - me) / (ml + me) : 0.0;
+      // discriminators in FP32, loop state and NCO words in double / integers
+      const float ip = v[2], qp = v[3];
+      const float e_phi = (ip == 0.f && qp == 0.f) ? 0.f : atanf(qp / ip) * 0.15915494309189535f;
+      const float me = hypotf(v[0], v[1]), ml = hypotf(v[4], v[5]);
+      const float e_tau = (me + ml > 0.f) ? (float)(1.0 - J.spacing / 2.0) * (ml - me) / (ml + me) : 0.f;
       gnss_track_rec r;
-      r.f_hz = (double)(int32_t)nco.wc * (double)J.fs / two32;
-      r.tau_chips = (double)((period - nco.P) % period) / two32;
-      r.ze[0] = (float)z[0];
-      r.ze[1] = (float)z[1];
-      r.zp[0] = (float)z[2];
-      r.zp[1] = (float)z[3];
-      r.zl[0] = (float)z[4];
-      r.zl[1] = (float)z[5];
-      r.e_phi = (float)e_phi;
-      r.e_tau = (float)e_tau;
+      r.f_hz = (double)(int32_t)nco.wc * J.fs / two32;
+      r.tau_chips = (double)(nco.P == 0 ? 0 : period - nco.P) / two32;
+      r.ze[0] = v[0];
+      r.ze[1] = v[1];
+      r.zp[0] = v[2];
+      r.zp[1] = v[3];
+      r.zl[0] = v[4];
+      r.zl[1] = v[5];
+      r.e_phi = e_phi;
+      r.e_tau = e_tau;
       r.status = 0;
       r.reserved = 0;
       rec[k] = r;
-      f_int += J.wn * J.wn * J.T * e_phi;
-      f = f_int + 2.0 * J.zeta * J.wn * e_phi;
-      s_nco.phi = nco.phi + (uint32_t)J.L * nco.wc;
-      s_nco.P = (nco.P + (int64_t)J.L * nco.wk) % period;
-      s_nco.status = track_words(J, f, e_tau, &s_nco.wc, &s_nco.wk);
+      f_int += J.wn * J.wn * J.T * (double)e_phi;
+      f = f_int + 2.0 * J.zeta * J.wn * (double)e_phi;
+      int64_t P = nco.P + (int64_t)J.L * nco.wk;
+      while (P >= period) P -= period;
+      nco_s.P = P;
+      nco_s.phi = nco.phi + (uint32_t)J.L * nco.wc;
+      nco_s.status = track_words(J, f, (double)e_tau, &nco_s.wc, &nco_s.wk);
     }
-    __syncthreads();
+    group_sync<TPC>();
   }
 }
 
@@ -284,10 +307,20 @@ extern "C" gnss_status gnss_track(gnss_plan* plan, const void* samples_dev, size
   J.T = (double)L / J.fs;
   J.b_dll = (double)cfg->dll_bw_hz;
   cudaStream_t cs = (cudaStream_t)stream;
-  if (plan->desc.format == GNSS_FMT_2BIT_IQ)
-    k_track<GNSS_FMT_2BIT_IQ><<<(unsigned)n_chan, kTrackThreads, 0, cs>>>(J, chans_dev, out_dev);
-  else
-    k_track<GNSS_FMT_I8_IQ><<<(unsigned)n_chan, kTrackThreads, 0, cs>>>(J, chans_dev, out_dev);
+  // Few channels: one CTA each (shortest time per interval); enough to fill
+  // the GPU: one warp each (no CTA barriers, 8 channels per CTA).
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
+  const bool per_warp = n_chan >= (size_t)4 * sms;
+  const int n = (int)n_chan;
+  const unsigned grid = per_warp ? (unsigned)((n_chan + 7) / 8) : (unsigned)n_chan;
+  if (plan->desc.format == GNSS_FMT_2BIT_IQ) {
+    if (per_warp) k_track<GNSS_FMT_2BIT_IQ, 32><<<grid, kTrackThreads, 0, cs>>>(J, chans_dev, n, out_dev);
+    else k_track<GNSS_FMT_2BIT_IQ, kTrackThreads><<<grid, kTrackThreads, 0, cs>>>(J, chans_dev, n, out_dev);
+  } else {
+    if (per_warp) k_track<GNSS_FMT_I8_IQ, 32><<<grid, kTrackThreads, 0, cs>>>(J, chans_dev, n, out_dev);
+    else k_track<GNSS_FMT_I8_IQ, kTrackThreads><<<grid, kTrackThreads, 0, cs>>>(J, chans_dev, n, out_dev);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e, "gnss_track");
   return GNSS_OK;

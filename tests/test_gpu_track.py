@@ -68,6 +68,25 @@ def test_track_1s_parity_and_lock(g):
         assert np.mean(last["zp"][:, 1] ** 2) < 0.1 * np.mean(last["zp"][:, 0] ** 2)
 
 
+def test_warp_per_channel_launch(g):
+    """With enough channels to fill the GPU (>= 4 per SM) each channel runs
+    on one warp: 80 copies of the 8 satellites' channels give identical
+    records copy to copy, and match the oracle."""
+    rec = siggen.track_1s()
+    prn, f, tau = siggen.track_starts(rec)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    reps = max(80, -(-4 * sms // len(prn)))
+    n_int = 200
+    out = _run(g, rec, np.tile(prn, reps), np.tile(f, reps), np.tile(tau, reps), n_int)
+    assert len(out) >= 4 * sms
+    for r in range(1, reps):
+        np.testing.assert_array_equal(out[r * len(prn):(r + 1) * len(prn)], out[:len(prn)])
+    x = oracle.unpack(rec.raw, rec.n_samples, rec.fmt)
+    for k in range(len(prn)):
+        ref = oracle.track(x, rec.fs, 1, n_int, oracle.ca_code(int(prn[k])), f[k], tau[k], 1.0, 15.0, 2.0)
+        _compare(out[k], ref)
+
+
 @pytest.mark.parametrize("fs,coh", [(2_048_000, 2), (16_384_000, 1)])
 def test_int8_rates_and_intervals(g, fs, coh):
     N = fs // 1000
