@@ -288,22 +288,31 @@ __device__ __forceinline__ void carrier_tile(const CarrierArgs& a, int tile, flo
   const int64_t fr = (((int64_t)f % fs) + fs) % fs;
   const int64_t r0 = (fr * ((int64_t)b * coh * N + j + sh)) % fs;
   const int64_t rs = (fr * T) % fs;
-  const int64_t rw = (fr * N) % fs;
   const float inv_fs = 1.f / (float)fs;
-  float s0, c0, ss, sc, sw, cw;
+  float s0, c0, ss, sc;
   sincospif(-2.f * (float)r0 * inv_fs, &s0, &c0);
   sincospif(-2.f * (float)rs * inv_fs, &ss, &sc);
-  sincospif(2.f * (float)rw * inv_fs, &sw, &cw);
   float2 car = make_float2(c0, s0);
   const float2 step = make_float2(sc, ss);
-  const float2 unwrap = make_float2(cw, sw);
   float2 v[E];
+  if (sh == 0) {  // uniform over the CTA
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int m = j + sh + T * r;
-    const bool wrapped = m >= N;
-    v[r] = c_mul(__ldg(z + (wrapped ? m - N : m)), wrapped ? c_mul(car, unwrap) : car);
-    car = c_mul(car, step);
+    for (int r = 0; r < E; ++r) {
+      v[r] = c_mul(__ldg(z + j + T * r), car);
+      car = c_mul(car, step);
+    }
+  } else {
+    const int64_t rw = (fr * N) % fs;
+    float sw, cw;
+    sincospif(2.f * (float)rw * inv_fs, &sw, &cw);
+    const float2 unwrap = make_float2(cw, sw);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int m = j + sh + T * r;
+      const bool wrapped = m >= N;
+      v[r] = c_mul(__ldg(z + (wrapped ? m - N : m)), wrapped ? c_mul(car, unwrap) : car);
+      car = c_mul(car, step);
+    }
   }
   int phase = 0;
   fft_block<N, E, false, Cfg<N>::DB>(v, j, buf0, buf1, phase);

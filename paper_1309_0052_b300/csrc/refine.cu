@@ -15,6 +15,9 @@
 //
 // Arithmetic: per-sample sums in FP32.  The code position is exact: with
 // n * 1023 = q N + rem, u_n = (q - tau_int) + (rem / N - tau_frac - 1/2).
+// The code sits in shared memory as a sign-bit table; each group of 8
+// samples reads one 64-bit window of it, so neighbouring threads (whose
+// chips are far apart) make no bank conflicts and no sample needs a modulo.
 // The carrier starts from a double-precision phase per thread chunk and
 // advances by a per-sample rotation.  Only the optimiser state (f, tau) is
 // kept in double.
@@ -73,9 +76,18 @@ __device__ __forceinline__ void load8(const uint8_t* __restrict__ base, int n0, 
 // One evaluation of P (and, with GRAD, the gradient) by the whole CTA.  The
 // window is cut into groups of 8 samples (L is a multiple of 8); thread t
 // sums the contiguous groups [t * gpt, (t + 1) * gpt) that exist.
+// Code of the candidate's PRN as a sign-bit table in shared memory: bit j is
+// set when chip j mod 1023 is -1, for j < 1023 + 65, so that a 64-bit window
+// read at any chip k < 1023 covers chips k .. k + 63 without a wrap.
+static constexpr int kRefBitWords = 34;
+
+struct CodeBits {
+  uint32_t w[kRefBitWords];
+  float scale;  // 1, or 0 when the PRN is not in the plan (P and gradient 0)
+};
+
 template <int T, int FMT, bool GRAD>
-__device__ EvalOut evaluate(const RefineJob& J, const float* __restrict__ chips, double f, double tau,
-                            float* red) {
+__device__ EvalOut evaluate(const RefineJob& J, const CodeBits& cb, double f, double tau, float* red) {
   const int groups = J.L / 8;
   const int gpt = (groups + T - 1) / T;
   const int g_end = min(groups, ((int)threadIdx.x + 1) * gpt);
@@ -106,6 +118,15 @@ __device__ EvalOut evaluate(const RefineJob& J, const float* __restrict__ chips,
   for (int base = 0; base < chunk; base += 8) {
     float xi[8], xq[8];
     load8<FMT>(J.samples, n0 + base, xi, xq);
+    // chips of the group: the position only grows, by under 32 chips over 8
+    // samples (N >= 256), so one 64-bit window from the group's first chip
+    // serves all of them (and each next chip)
+    const int kf = q - ti + (int)floorf(fmaf((float)rem, invN, -tf));
+    int km = kf % 1023;
+    km += (km < 0) ? 1023 : 0;
+    const uint32_t lo = __funnelshift_r(cb.w[km >> 5], cb.w[(km >> 5) + 1], km & 31);
+    const uint32_t hi = __funnelshift_r(cb.w[(km >> 5) + 1], cb.w[(km >> 5) + 2], km & 31);
+    const uint64_t win = ((uint64_t)hi << 32) | lo;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       // wiped sample w = x e^{-j theta}
@@ -117,10 +138,10 @@ __device__ EvalOut evaluate(const RefineJob& J, const float* __restrict__ chips,
       const float fl = floorf(ufrac);
       k += (int)fl;
       const float a = ufrac - fl;
-      int i0 = k % 1023;
-      i0 += (i0 < 0) ? 1023 : 0;
-      const int i1 = (i0 == 1022) ? 0 : i0 + 1;
-      const float c0v = chips[i0], c1v = chips[i1];
+      const uint32_t rel = (uint32_t)(k - kf);
+      const uint32_t b0 = (uint32_t)(win >> rel) & 1u, b1 = (uint32_t)(win >> (rel + 1u)) & 1u;
+      const float c0v = __int_as_float(0x3f800000 | (int)(b0 << 31));  // +-1
+      const float c1v = __int_as_float(0x3f800000 | (int)(b1 << 31));
       const float sl = c1v - c0v;
       const float ct = fmaf(a, sl, c0v);
       zr = fmaf(wr, ct, zr);
@@ -144,15 +165,15 @@ __device__ EvalOut evaluate(const RefineJob& J, const float* __restrict__ chips,
     }
   }
   EvalOut o;
-  zr = block_sum<T>(zr, red);
-  zi = block_sum<T>(zi, red);
+  zr = block_sum<T>(zr * cb.scale, red);
+  zi = block_sum<T>(zi * cb.scale, red);
   o.P = zr * zr + zi * zi;
   o.gf = o.gt = 0.f;
   if constexpr (GRAD) {
-    fr = block_sum<T>(fr, red);
-    fi = block_sum<T>(fi, red);
-    tr = block_sum<T>(tr, red);
-    tii = block_sum<T>(tii, red);
+    fr = block_sum<T>(fr * cb.scale, red);
+    fi = block_sum<T>(fi * cb.scale, red);
+    tr = block_sum<T>(tr * cb.scale, red);
+    tii = block_sum<T>(tii * cb.scale, red);
     // dz/df -> (-j 2 pi / fs) sum (n - L/2) w ctilde = (2 pi / fs) (fi - j fr)
     const float g = (float)(2.0 * 3.14159265358979323846 / J.fs);
     const float dfr = g * fi, dfi = -g * fr;
@@ -163,9 +184,16 @@ __device__ EvalOut evaluate(const RefineJob& J, const float* __restrict__ chips,
 }
 
 template <int T>
-__device__ __forceinline__ void load_chips(const RefineJob& J, int prn, float* chips) {
+__device__ __forceinline__ void load_chips(const RefineJob& J, int prn, CodeBits& cb) {
   const int idx = (prn >= 1 && prn <= 32) ? J.prn_index[prn] : -1;
-  for (int i = threadIdx.x; i < 1023; i += T) chips[i] = idx >= 0 ? (float)J.codes[idx * 1023 + i] : 0.f;
+  for (int w = threadIdx.x; w < kRefBitWords; w += T) {
+    uint32_t v = 0;
+    if (idx >= 0)
+      for (int b = 0; b < 32; ++b)
+        if (J.codes[idx * 1023 + (32 * w + b) % 1023] < 0) v |= 1u << b;
+    cb.w[w] = v;
+  }
+  if (threadIdx.x == 0) cb.scale = idx >= 0 ? 1.f : 0.f;
   __syncthreads();
 }
 
@@ -174,7 +202,7 @@ template <int T, int FMT>
 __global__ void __launch_bounds__(T) k_refine_eval(RefineJob J, const int* __restrict__ prn, const double* __restrict__ f,
                                                   const double* __restrict__ tau, float* __restrict__ P,
                                                   float* __restrict__ dPdf, float* __restrict__ dPdtau) {
-  __shared__ float chips[1023];
+  __shared__ CodeBits chips;
   __shared__ float red[32];
   load_chips<T>(J, prn[blockIdx.x], chips);
   const EvalOut o = evaluate<T, FMT, true>(J, chips, f[blockIdx.x], tau[blockIdx.x], red);
@@ -208,7 +236,7 @@ __global__ void __launch_bounds__(T) k_refine_eval(RefineJob J, const int* __res
 template <int T, int FMT>
 __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate* __restrict__ cands, int max_iter,
                                              double search_hz, gnss_refined* __restrict__ out) {
-  __shared__ float chips[1023];
+  __shared__ CodeBits chips;
   __shared__ float red[32];
   const gnss_candidate c = cands[blockIdx.x];
   load_chips<T>(J, c.prn, chips);
