@@ -667,6 +667,49 @@ def _oracle_sample(rec, threads, every=CPU_SAMPLE_EVERY):
     return _cells(32, len(dopp), rec.N, rec.n_blocks, rec.coh_ms)
 
 
+def cpu_fft_acquire(rec, threads, every=CPU_SAMPLE_EVERY):
+    """Optimised CPU acquisition beside the plain oracle, with the paper's CPU
+    lessons (Section 4: persistent worker threads, dynamic scheduling,
+    vectorised FFT library): a pool of 'threads' workers takes Doppler bins
+    as they free up; per bin, the coherent fold uses the per-millisecond
+    carrier constant (so only N samples per block take a carrier), then a
+    complex64 FFT of every block, the conj-multiply with all 32 code spectra,
+    a batched IFFT (scipy.fft / pocketfft), |.|^2, the half-bit set sums and
+    the per-PRN peak.  FP32 like the GPU path.  Runs every 'every'-th
+    Doppler bin; returns (cells, per-set per-PRN peaks)."""
+    import concurrent.futures as cf
+    import scipy.fft as sf
+    N, coh, B, fs = rec.N, rec.coh_ms, rec.n_blocks, rec.fs
+    L = coh * N
+    raw = np.frombuffer(np.asarray(rec.raw).tobytes(), np.uint8)[: (B * L + 1) // 2]
+    lv = np.array([-3, -1, 1, 3], np.float32)
+    x = np.empty(2 * len(raw), np.complex64)
+    x[0::2] = lv[raw & 3] + 1j * lv[(raw >> 2) & 3]
+    x[1::2] = lv[(raw >> 4) & 3] + 1j * lv[(raw >> 6) & 3]
+    X3 = x[: B * L].reshape(B, coh, N)
+    table = siggen.chip_table()
+    m = np.arange(N)
+    conjC = np.conj(sf.fft(table[:, (m * 1023) // N].astype(np.complex64), axis=-1)).astype(np.complex64)
+    sets = 2 if rec.half_bit else 1
+    bm = (np.arange(B, dtype=np.int64)[:, None] * L + m[None, :])  # sample index of (b, m)
+
+    def one_bin(f):
+        f = int(f)
+        w = np.exp(-2j * np.pi * ((f * np.arange(coh)) % 1000) / 1000.0).astype(np.complex64)
+        car = np.exp(-2j * np.pi * ((f * bm) % fs) / fs).astype(np.complex64)
+        y = np.einsum("i,bim->bm", w, X3) * car
+        Y = sf.fft(y, axis=-1)
+        R = sf.ifft(Y[None] * conjC[:, None, :], axis=-1)           # [P, B, N]
+        pw = R.real * R.real + R.imag * R.imag
+        return np.stack([pw[:, s::sets].sum(axis=1).max(axis=1) for s in range(sets)])
+
+    dopp = rec.dopp_hz[::every]
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        peaks = list(ex.map(one_bin, dopp))
+    best = np.max(np.stack(peaks), axis=0)
+    return _cells(32, len(dopp), N, B, coh), best
+
+
 def cpu_baseline(rec, args):
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
@@ -680,11 +723,24 @@ def cpu_baseline(rec, args):
     t1 = time.perf_counter()
     cells1 = _oracle_sample(rec, 1, every=27)
     dt1 = time.perf_counter() - t1
+    # optimised CPU pipeline (scipy.fft on all cores, complex64) on the same sample
+    cpu_fft_acquire(rec, threads, every=27)  # warm the FFT plans
+    t2 = time.perf_counter()
+    cells2, reps2 = 0, 0
+    while reps2 < 1 or (time.perf_counter() - t2 < 2.0 and reps2 < 50):
+        cells2 += cpu_fft_acquire(rec, threads)[0]
+        reps2 += 1
+    dt2 = time.perf_counter() - t2
     return {"value": cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d x (27 of 81 Doppler bins, all 32 PRNs, 10 blocks, both sets), FP64 C oracle, "
                       "%d threads over Doppler rows, %.1f s wall" % (reps, threads, dt),
             "single_thread": {"value": cells1 / dt1, "unit": UNIT, "cores": 1,
-                              "sample": "3 of 81 Doppler bins, all 32 PRNs, 10 blocks, both sets, %.1f s" % dt1}}
+                              "sample": "3 of 81 Doppler bins, all 32 PRNs, 10 blocks, both sets, %.1f s" % dt1},
+            "optimised_cpu": {"value": cells2 / dt2, "unit": UNIT, "cores": threads,
+                              "kind": "numpy + scipy.fft (pocketfft) complex64 pipeline, %d persistent workers "
+                                      "taking Doppler bins as they free up" % threads,
+                              "sample": "%d x (27 of 81 Doppler bins, all 32 PRNs, 10 blocks, both sets), %.1f s"
+                                        % (reps2, dt2)}}
 
 
 def run_reference(args):
