@@ -226,6 +226,28 @@ typedef struct {
  * GNSS_ENOMEM, GNSS_ECUDA. */
 GNSS_API gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t scratch_budget, void* stream);
 
+/* Second-stage fine Doppler search around coarse detections.  For each of
+ * the n_det host records in det (typically the detected ones of a
+ * gnss_acquire on this plan and recording), the acquisition of Section 3,
+ * Fig. 2 is run again for that PRN alone on a grid zoom times finer,
+ * spanning +-span coarse steps around the record's Doppler:
+ *   f_k = det.dopp_hz + (k - span * zoom) * dopp_step_hz / zoom,
+ *   k < 2 * span * zoom + 1,
+ * with the plan's sample rate, coherent length, blocks, format, flags and
+ * threshold, in one batched launch over all detections (the code spectra are
+ * the plan's own).  out_dev[i] (device) receives the record of detection i
+ * on its fine grid (dopp_bin indexes that grid); surface_dev, when not NULL,
+ * receives detection i's surface [n_sets][1][2 span zoom + 1][N] at offset
+ * i * n_sets * (2 span zoom + 1) * N floats.  Each record equals what
+ * gnss_acquire_device gives for a plan with that fine grid and that PRN.
+ * Asynchronous on 'stream'.  Errors: GNSS_EINVAL (NULL arguments, zoom not
+ * in [2, 1000] or not dividing dopp_step_hz, span not in [1, 100], a PRN not
+ * in the plan, more than 4096 detections, any invalid request),
+ * GNSS_ENOMEM, GNSS_ECUDA. */
+GNSS_API gnss_status gnss_acquire_zoom(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                       const gnss_detection* det, size_t n_det, uint32_t zoom, uint32_t span,
+                                       gnss_detection* out_dev, float* surface_dev, void* stream);
+
 /* Acquisition that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory at
  * request time -- services that must keep a fixed device footprint after

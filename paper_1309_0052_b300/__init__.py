@@ -99,6 +99,7 @@ _SIGS = {
                     _st),
     "gnss_refine_device": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_double, _P, _P], _st),
     "gnss_acquire_batch": ([_P, C.c_size_t, C.c_size_t, _P], _st),
+    "gnss_acquire_zoom": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.c_uint32, C.c_uint32, _P, _P, _P], _st),
     "gnss_track": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.POINTER(TrackConfig), _P, _P], _st),
     "gnss_server_create": ([_P, C.POINTER(_P)], _st),
     "gnss_server_destroy": ([_P], _st),
@@ -297,6 +298,23 @@ class Plan:
         check(load().gnss_refine_eval(self._h, _ptr(samples_dev), n_samples, coh_ms, _ptr(prn_dev), _ptr(f_dev),
                                       _ptr(tau_dev), prn_dev.numel(), _ptr(P_dev), _ptr(dPdf_dev),
                                       _ptr(dPdtau_dev), _stream_ptr(stream)), "gnss_refine_eval")
+
+    def zoom(self, samples_dev, n_samples: int, detections, zoom: int = 5, span: int = 1, surface=None,
+             stream=None) -> np.ndarray:
+        """gnss_acquire_zoom: fine Doppler search (grid step / zoom over +-span
+        steps) around each record of 'detections' (numpy DETECTION_DTYPE).
+        Returns the fine records; synchronises the stream."""
+        det = np.ascontiguousarray(detections, DETECTION_DTYPE)
+        import torch  # device memory for the records
+        out = torch.zeros(max(len(det), 1) * DETECTION_DTYPE.itemsize, dtype=torch.uint8,
+                          device=samples_dev.device)
+        check(load().gnss_acquire_zoom(self._h, _ptr(samples_dev), n_samples, det.ctypes.data, len(det), zoom,
+                                       span, _ptr(out), _ptr(surface), _stream_ptr(stream)), "gnss_acquire_zoom")
+        if stream is not None:
+            stream.synchronize()
+        else:
+            torch.cuda.synchronize()
+        return detections_from_bytes(out.cpu().numpy())[: len(det)]
 
     def track(self, samples_dev, n_samples: int, chans_dev, n_chan: int, out_dev, n_int: int, coh_ms: int = 1,
               spacing: float = 1.0, pll_bw_hz: float = 15.0, dll_bw_hz: float = 1.0, stream=None) -> None:

@@ -169,6 +169,30 @@ static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_s
 
 }  // namespace gnss
 
+namespace gnss {
+
+// Fold groups: the per-millisecond wipe-off factor exp(-j 2 pi (f i mod 1000) / 1000)
+// depends on f only through f mod 1000 (and not at all with one coherent ms).
+int fold_groups(const gnss_plan_desc& d, std::vector<int>& group, std::vector<int>& gkey) {
+  group.assign(d.n_dopp, 0);
+  gkey.clear();
+  for (uint32_t k = 0; k < d.n_dopp; ++k) {
+    const int64_t f = (int64_t)d.dopp_min_hz + (int64_t)k * d.dopp_step_hz;
+    const int key = d.coh_ms == 1 ? 0 : (int)(((f % 1000) + 1000) % 1000);
+    int gi = -1;
+    for (size_t q = 0; q < gkey.size(); ++q)
+      if (gkey[q] == key) gi = (int)q;
+    if (gi < 0) {
+      gi = (int)gkey.size();
+      gkey.push_back(key);
+    }
+    group[k] = gi;
+  }
+  return (int)gkey.size();
+}
+
+}  // namespace gnss
+
 using namespace gnss;
 
 extern "C" {
@@ -204,22 +228,8 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   p->excl = (N + 1022) / 1023;
   for (int prn = 1; prn <= 32; ++prn)
     if (d.prn_mask >> (prn - 1) & 1ull) p->prns[p->P++] = prn;
-  // Fold groups: the per-millisecond wipe-off factor exp(-j 2 pi (f i mod 1000) / 1000)
-  // depends on f only through f mod 1000 (and not at all with one coherent ms).
-  std::vector<int> group(p->D), gkey;
-  for (int k = 0; k < p->D; ++k) {
-    const int64_t f = (int64_t)d.dopp_min_hz + (int64_t)k * d.dopp_step_hz;
-    const int key = d.coh_ms == 1 ? 0 : (int)(((f % 1000) + 1000) % 1000);
-    int gi = -1;
-    for (size_t q = 0; q < gkey.size(); ++q)
-      if (gkey[q] == key) gi = (int)q;
-    if (gi < 0) {
-      gi = (int)gkey.size();
-      gkey.push_back(key);
-    }
-    group[k] = gi;
-  }
-  p->G = (int)gkey.size();
+  std::vector<int> group, gkey;
+  p->G = fold_groups(d, group, gkey);
   cudaError_t e = cudaGetDevice(&p->device);
   cudaStream_t st = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "gnss.h"
 
@@ -149,6 +150,10 @@ gnss_status fail_status(gnss_status st, const std::string& msg);
 gnss_status cuda_status(cudaError_t e, const char* where);
 gnss_status check_plan_device(const gnss_plan* plan);
 gnss_status scratch_alloc(int dev, size_t bytes, cudaStream_t stream, void** out);
+
+// Fold groups of a plan's Doppler grid (bins sharing f mod 1000; one group
+// when coh_ms == 1): group[d] for every bin, gkey[g] = f mod 1000.  Returns G.
+int fold_groups(const gnss_plan_desc& d, std::vector<int>& group, std::vector<int>& gkey);
 
 // Last-error message (thread-local), set by the C-ABI layer.
 void set_error(const std::string& msg);

@@ -1,0 +1,82 @@
+"""Second-stage fine Doppler search (gnss_acquire_zoom) against the FP64
+oracle: the detections of the 100 ms workload, each searched again on a grid
+five times finer over +-1 coarse step.  Every zoomed record and surface must
+match the oracle's acquisition on that fine grid and PRN, equal a plan built
+with that grid by hand, and move the Doppler estimate closer to the truth."""
+import numpy as np
+import pytest
+
+import oracle
+import siggen
+from parity import compare_detections, compare_surfaces
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1309_0052_b300 as g
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return g
+
+
+@pytest.fixture(scope="module")
+def coarse(g):
+    rec = siggen.weak_100ms()
+    plan = g.Plan.for_recording(rec)
+    raw = torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda()
+    det = plan.acquire(raw, rec.n_samples)
+    return rec, plan, raw, det[det["detected"] == 1]
+
+
+def test_zoom_matches_oracle_and_explicit_plan(g, coarse):
+    rec, plan, raw, det = coarse
+    assert len(det) >= 3
+    zoom, span = 5, 1
+    D = 2 * span * zoom + 1
+    surf = torch.zeros((len(det), plan.n_sets, 1, D, plan.N), dtype=torch.float32, device="cuda")
+    fine = plan.zoom(raw, rec.n_samples, det, zoom, span, surface=surf)
+    S_all = surf.cpu().numpy()
+    step = rec.dopp_step_hz // zoom
+    for i, d in enumerate(det):
+        p = int(d["prn"])
+        grid = int(d["dopp_hz"]) - span * rec.dopp_step_hz + step * np.arange(D)
+        ref_det, ref_S = oracle.acquire(rec.raw, rec.n_samples, rec.fmt, rec.fs, rec.coh_ms, grid, [p],
+                                        half_bit=True, nthreads=8)
+        compare_surfaces(S_all[i], ref_S)
+        assert compare_detections(fine[i:i + 1], ref_det, ref_S) == 0
+        assert int(fine[i]["dopp_hz"]) == int(grid[int(fine[i]["dopp_bin"])])
+        # the same records and surfaces as a plan created with that grid
+        fp = g.Plan(rec.fs, rec.coh_ms, int(grid[0]), step, D, prns=[p], half_bit=True, fmt=rec.fmt)
+        out = torch.zeros(28, dtype=torch.uint8, device="cuda")
+        s2 = torch.zeros(fp.surface_shape(), dtype=torch.float32, device="cuda")
+        fp.acquire_device(raw, rec.n_samples, out, surface=s2)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(g.detections_from_bytes(out.cpu().numpy()), fine[i:i + 1])
+        np.testing.assert_array_equal(s2.cpu().numpy(), S_all[i])
+
+
+def test_zoom_moves_doppler_toward_truth(g, coarse):
+    rec, plan, raw, det = coarse
+    fine = plan.zoom(raw, rec.n_samples, det, 5, 1)
+    truth = {s.prn: s.dopp_hz + 0.5 * s.dopp_rate * 0.05 for s in rec.sats}  # mid-recording
+    ec = np.array([abs(int(d["dopp_hz"]) - truth[int(d["prn"])]) for d in det])
+    ez = np.array([abs(int(d["dopp_hz"]) - truth[int(d["prn"])]) for d in fine])
+    assert np.all(ez <= 25.0)                       # within the fine grid's half step, plus scalloping
+    assert ez.mean() < 0.5 * ec.mean()
+    dcp = (fine["code_phase"].astype(int) - det["code_phase"].astype(int) + plan.N // 2) % plan.N - plan.N // 2
+    assert np.all(np.abs(dcp) <= 1)
+
+
+def test_zoom_rejects(g, coarse):
+    rec, plan, raw, det = coarse
+    with pytest.raises(g.GnssError) as e:
+        plan.zoom(raw, rec.n_samples, det, 3, 1)  # 250 Hz is not a multiple of 3
+    assert e.value.status == g.EINVAL
+    sub = g.Plan.for_recording(rec, prns=[p for p in range(1, 33) if p != int(det[0]["prn"])])
+    with pytest.raises(g.GnssError) as e:
+        sub.zoom(raw, rec.n_samples, det[:1], 5, 1)  # PRN not in that plan
+    assert e.value.status == g.EINVAL
+    assert len(plan.zoom(raw, rec.n_samples, det[:0], 5, 1)) == 0
