@@ -498,8 +498,9 @@ GNSS_API gnss_status gnss_server_get_stats(gnss_server* srv, gnss_server_stats* 
 GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
 
 /* Launch-shape autotuner of the correlate kernel (the FFT-heavy stage).  It
- * can hold 16 or 32 FFT elements per thread (N/16 or N/32 threads per FFT;
- * 32 needs N >= 1024, 16 needs N <= 16384), and with 16 it can stage the
+ * can hold 8, 16 or 32 FFT elements per thread (N/8, N/16 or N/32 threads
+ * per FFT; 8 needs N <= 8192 and runs radix-8 passes, 32 needs N >= 1024,
+ * 16 needs N <= 16384), and with 16 it can stage the
  * next block's spectrum into shared memory by a bulk TMA copy while the
  * current block is transformed (variant code 16 | GNSS_TUNE_STAGED, offered
  * where the CTA's shared memory still fits: N <= 8192).  With

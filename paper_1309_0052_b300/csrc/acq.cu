@@ -56,7 +56,7 @@ template <int N>
 struct Cfg {
   static constexpr int E = N >= 16384 ? 32 : 16;
   static constexpr int T = N / E;
-  static constexpr bool TWC = (E == 16);                        // twiddle bases cached in registers
+  static constexpr bool TWC = (E <= 16);                        // twiddle bases cached in registers
   static constexpr size_t buf_bytes = sizeof(float2) * FftShape<N>::smem_elems;
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
   static constexpr size_t smem = (DB ? 2 : 1) * buf_bytes;
@@ -69,12 +69,13 @@ struct Cfg {
 template <int N, int E, bool ST = false>
 struct XCfg {
   static constexpr int T = N / E;
-  static constexpr bool TWC = (E == 16);                        // twiddle bases cached in registers
+  static constexpr bool TWC = (E <= 16);                        // twiddle bases cached in registers
   static constexpr size_t buf_bytes = sizeof(float2) * FftShape<N>::smem_elems;
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
   static constexpr size_t stage_off = (DB ? 2 : 1) * buf_bytes;
   static constexpr size_t smem = stage_off + (ST ? sizeof(float2) * N : 0);
-  static constexpr int MINB = T <= 256 ? 2 : 1;
+  // two CTAs per SM: up to 128 registers at 256 threads, 64 at 512 (E = 8)
+  static constexpr int MINB = (T <= 256 || (E <= 8 && T <= 512)) ? 2 : 1;
   static_assert(stage_off % 16 == 0, "bulk copies need a 16-byte aligned destination");
 };
 
@@ -756,7 +757,7 @@ static bool stage_fits(int N) {
 
 bool xcorr_valid_e(int N, int code) {
   if (code == (16 | (int)GNSS_TUNE_STAGED)) return N / 16 <= 1024 && stage_fits(N);
-  return (code == 16 && N / 16 <= 1024) || (code == 32 && N >= 1024);
+  return (code == 16 && N / 16 <= 1024) || (code == 32 && N >= 1024) || (code == 8 && N / 8 <= 1024);
 }
 
 int xcorr_variant(int N) {
@@ -797,6 +798,9 @@ static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t s
   const int v = xcorr_variant(N);
   if constexpr (N >= 1024) {
     if (v == 32) return xcorr_ne<N, 32, false>(s, a, stream);
+  }
+  if constexpr (N / 8 <= 1024) {
+    if (v == 8) return xcorr_ne<N, 8, false>(s, a, stream);
   }
   if constexpr (StageFits<N>::value) {
     if (v == (16 | (int)GNSS_TUNE_STAGED)) return xcorr_ne<N, 16, true>(s, a, stream);
@@ -888,6 +892,9 @@ static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
   const int v = xcorr_variant(N);
   if constexpr (N >= 1024) {
     if (v == 32) return xcorr_batch_ne<N, 32, false>(g, stream);
+  }
+  if constexpr (N / 8 <= 1024) {
+    if (v == 8) return xcorr_batch_ne<N, 8, false>(g, stream);
   }
   if constexpr (StageFits<N>::value) {
     if (v == (16 | (int)GNSS_TUNE_STAGED)) return xcorr_batch_ne<N, 16, true>(g, stream);

@@ -217,12 +217,14 @@ struct FftShape {
   static constexpr int smem_elems = N + N / 16;
 };
 
-// Radix of the pass with sub-transform size NS: 16 while 16 divides what is
-// left of N, then the remainder (2, 4 or 8).
-template <int N, int NS>
+// Radix of the pass with sub-transform size NS: RMAX (16, or E when a
+// thread holds fewer than 16 elements) while RMAX divides what is left of
+// N, then the remainder.
+template <int N, int NS, int E = 16>
 struct PassRadix {
+  static constexpr int rmax = E < 16 ? E : 16;
   static constexpr int rem = N / NS;
-  static constexpr int value = rem >= 16 ? 16 : rem;
+  static constexpr int value = rem >= rmax ? rmax : rem;
 };
 
 // One butterfly set of a pass (thread-local), twiddled and transformed.
@@ -264,13 +266,16 @@ __device__ __forceinline__ void pass_compute(float2 (&v)[E], int j) {
 }
 
 // Scatter the pass outputs to shared memory at their Stockham positions.
-// NS is 1 or a multiple of 16 (radix-16 passes come first), and for NS = 1
-// base = R J keeps base mod 16 + t < 16; either way
+// NS is 1, 8 or a multiple of 16 (radix-16 passes come first; radix-8
+// transforms have NS = 1, 8, 64, ...).  For NS = 1, base = R J keeps
+// base mod 16 + t < 16; for NS = 8, base = 64 (J / 8) + J mod 8 has
+// base mod 16 < 8, so base + 8 t crosses a multiple of 16 exactly t / 2
+// times; for NS a multiple of 16 the steps are whole.  In every case
 // pad16(base + t NS) = pad16(base) + t NS + (t NS) / 16, so each store is one
 // per-butterfly address plus a compile-time offset.
 template <int N, int E, int R, int NS>
 __device__ __forceinline__ void pass_store(const float2 (&v)[E], int j, float2* __restrict__ buf) {
-  static_assert(NS == 1 || NS % 16 == 0, "pass order: radix-16 passes first");
+  static_assert(NS == 1 || NS % 16 == 0 || (NS == 8 && R == 8), "pass order: radix-16 (or 8) passes first");
   constexpr int T = N / E;
   constexpr int Q = E / R;
 #pragma unroll
@@ -311,7 +316,7 @@ __device__ __forceinline__ void scatter_regs(const float2 (&v)[E], int j, float2
 // read.  Every thread of the CTA must call this.
 template <int N, int E, bool INV, bool DOUBLE_BUF, int NS = 1>
 __device__ __forceinline__ void fft_block(float2 (&v)[E], int j, float2* buf0, float2* buf1, int& phase) {
-  constexpr int R = PassRadix<N, NS>::value;
+  constexpr int R = PassRadix<N, NS, E>::value;
   pass_compute<N, E, R, NS, INV>(v, j);
   if constexpr (NS * R < N) {
     float2* buf = (DOUBLE_BUF && phase) ? buf1 : buf0;
@@ -416,7 +421,7 @@ struct TwApply {
 // Twiddle bases of every pass of an N-point transform for thread j.
 template <int N, int E, bool INV, int NS = 1>
 struct FftTw {
-  static constexpr int R = PassRadix<N, NS>::value;
+  static constexpr int R = PassRadix<N, NS, E>::value;
   static constexpr int Q = E / R;
   static constexpr int T = N / E;
   typename TwSel<R>::type tw[NS > 1 ? Q : 1];
@@ -475,7 +480,7 @@ struct NoHook {
 template <int N, int E, bool INV, bool DOUBLE_BUF, int NS = 1, typename Hook = NoHook>
 __device__ __forceinline__ void fft_block_tw(float2 (&v)[E], int j, float2* buf0, float2* buf1, int& phase,
                                              const FftTw<N, E, INV, NS>& tw, const Hook& hook = Hook()) {
-  constexpr int R = PassRadix<N, NS>::value;
+  constexpr int R = PassRadix<N, NS, E>::value;
   pass_compute_tw<N, E, R, NS, INV>(v, tw);
   if constexpr (NS * R < N) {
     float2* buf = (DOUBLE_BUF && phase) ? buf1 : buf0;

@@ -40,6 +40,8 @@ def _valid(N):
         v.append(32)
     if N <= 8192:
         v.append(16 | STAGED)
+    if N <= 8192:
+        v.append(8)
     return v
 
 
