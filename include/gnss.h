@@ -255,7 +255,8 @@ GNSS_API gnss_status gnss_acquire_zoom(gnss_plan* plan, const void* samples_dev,
  * allocator, a reserved arena) owns the device memory, so that cudaMalloc or
  * cudaMallocAsync is forbidden or may fail.  It computes exactly what
  * gnss_acquire_device computes, with the same kernels, but takes its scratch
- * (n_dopp * blocks * N * 8 bytes of spectra plus the per-row statistics)
+ * (folded blocks, blocks * N * 8 bytes of spectra per class of bins a whole
+ * kHz apart -- per bin with GNSS_CODE_DOPPLER -- and the per-row statistics)
  * from one fixed 32 MiB device array inside the library, which every GPU
  * that loads the library holds until the process exits.
  *  - Inputs and outputs are the caller's, as in gnss_acquire_device:

@@ -265,7 +265,9 @@ __device__ __forceinline__ int64_t code_doppler_sigma(int f, int b, int64_t L) {
   return q;
 }
 
-// k_carrier_fft: one CTA per (Doppler d, block b), tile = d * B + b.  Loads the
+// k_carrier_fft: one CTA per (Doppler d, block b), tile = d * B + b -- or per
+// (spectrum class, block) when bins a whole number of kHz apart share one
+// spectrum (the correlate kernel reads it shifted).  Loads the
 // folded block of its group in the FFT's register layout, multiplies by the
 // carrier exp(-j 2 pi ((f (bL + m)) mod fs) / fs) -- exact integer phase for
 // r = 0, then a rotation by T samples per r -- and runs the forward FFT:
@@ -281,9 +283,9 @@ __device__ __forceinline__ void carrier_tile(const CarrierArgs& a, int tile, flo
   float2* buf1 = Cfg<N>::DB ? sm + FftShape<N>::smem_elems : sm;
   const int fs = a.fs, coh = a.coh, B = a.B;
   const int j = threadIdx.x;
-  const int d = tile / B, b = tile % B;
-  const int f = a.dopp_min + d * a.dopp_step;
-  const float2* z = a.Z + ((size_t)a.group[d] * B + b) * N;
+  const int d = tile / B, b = tile % B;  // d: a bin, or a spectrum class
+  const int f = a.cls_fgroup ? a.cls_base[d] : a.dopp_min + d * a.dopp_step;
+  const float2* z = a.Z + ((size_t)(a.cls_fgroup ? a.cls_fgroup[d] : a.group[d]) * B + b) * N;
   int sh = 0;
   if (a.code_dopp) sh = (int)(((-code_doppler_sigma(f, b, (int64_t)coh * N)) % N + N) % N);
   const int64_t fr = (((int64_t)f % fs) + fs) % fs;
@@ -494,11 +496,12 @@ struct StageIssue {
 // (once the stage's barrier phase has completed) and the copy of the next
 // block is issued after the IFFT's first barrier.
 template <int N, int E, bool DB, bool TWC, bool ST>
-__device__ __forceinline__ void corr_block(const float2* __restrict__ y, const float2* __restrict__ cp, int j,
-                                           float2* buf0, float2* buf1, int& phase, FftTw<N, E, true>& tw,
+__device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh, const float2* __restrict__ cp,
+                                           int j, float2* buf0, float2* buf1, int& phase, FftTw<N, E, true>& tw,
                                            float (&acc)[E], const StageIssue& next, uint32_t& parity,
                                            bool& stage_ok) {
   constexpr int T = N / E;
+  const int js = j + ksh;  // element k of the bin's spectrum is element k + ksh of the row
   if constexpr (TWC) tw.launder();
   // Re-read the code spectrum from L1 every block: hoisting these 16 loads
   // out of the block loop would pin 32 registers and force spills.
@@ -507,16 +510,21 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, const f
   if constexpr (ST) {
     if (!stage_wait(next.mbar, parity)) stage_ok = false;
     parity ^= 1u;
-    const float2* stg = next.stg;
+    // ksh < 16 <= T (spectrum classes are cut so): only the last element can wrap
+    const float2* ys = next.stg + js;
 #pragma unroll
-    for (int r = 0; r < E; ++r) v[r] = c_mulconj(stg[j + T * r], __ldg(cp + j + T * r));
+    for (int r = 0; r < E - 1; ++r) v[r] = c_mulconj(ys[T * r], __ldg(cp + j + T * r));
+    const int last = js + T * (E - 1);
+    v[E - 1] = c_mulconj(next.stg[last >= N ? last - N : last], __ldg(cp + j + T * (E - 1)));
     fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw, next);
   } else {
+    // Y streams from L2 (not kept in L1); the code spectrum stays L1-resident.
+    // ksh < 16 <= T (spectrum classes are cut so): only the last element can wrap
+    const float2* ys = y + js;
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      // Y streams from L2 (not kept in L1); the code spectrum stays L1-resident
-      v[r] = c_mulconj(__ldcg(y + j + T * r), __ldg(cp + j + T * r));
-    }
+    for (int r = 0; r < E - 1; ++r) v[r] = c_mulconj(__ldcg(ys + T * r), __ldg(cp + j + T * r));
+    const int last = js + T * (E - 1);
+    v[E - 1] = c_mulconj(__ldcg(y + (last >= N ? last - N : last)), __ldg(cp + j + T * (E - 1)));
     if constexpr (TWC) fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw);
     else fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
   }
@@ -596,7 +604,10 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   const int j = threadIdx.x;
   const int p = tile % a.P, d = tile / a.P;
   const float2* cp = a.cspec + (size_t)p * N;
-  const float2* yd = a.Y + (size_t)d * a.B * N;
+  // bin d's spectrum: its own row, or its class's row read K bins further
+  // (Y_{f + 1000 K}[k] = Y_f[k + K]: a whole kHz is one bin of a 1 ms FFT)
+  const float2* yd = a.Y + (size_t)(a.bin_cls ? __ldg(a.bin_cls + d) : d) * a.B * N;
+  const int ksh = a.bin_shift ? __ldg(a.bin_shift + d) : 0;
   StageIssue next{reinterpret_cast<float2*>(reinterpret_cast<char*>(sm) + X::stage_off), nullptr, &s_mbar,
                   (uint32_t)(sizeof(float2) * N), j};
   uint32_t parity = 0;
@@ -624,7 +635,7 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
         if (nb >= a.B) nb = set + 1 < S ? set + 1 : a.B;
         next.src = nb < a.B ? yd + (size_t)nb * N : nullptr;
       }
-      corr_block<N, E, DB, TWC, ST>(yd + (size_t)b * N, cp, j, buf0, buf1, phase, tw, acc, next, parity,
+      corr_block<N, E, DB, TWC, ST>(yd + (size_t)b * N, ksh, cp, j, buf0, buf1, phase, tw, acc, next, parity,
                                     stage_ok);
     }
     // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
@@ -727,7 +738,7 @@ static cudaError_t wipe_fft_n(const AcqShape& s, const uint8_t* d_samples, const
   if (e != cudaSuccess) return e;
   e = set_smem(k_carrier_fft<N>, Cfg<N>::smem);
   if (e != cudaSuccess) return e;
-  k_carrier_fft<N><<<s.D * s.B, Cfg<N>::T, Cfg<N>::smem, stream>>>(carrier_args(s, d_group, d_Z, d_Y));
+  k_carrier_fft<N><<<(s.C ? s.C : s.D) * s.B, Cfg<N>::T, Cfg<N>::smem, stream>>>(carrier_args(s, d_group, d_Z, d_Y));
   return cudaGetLastError();
 }
 
@@ -832,6 +843,8 @@ CarrierArgs carrier_args(const AcqShape& s, const int* d_group, const float2* d_
   a.dopp_min = s.dopp_min;
   a.dopp_step = s.dopp_step;
   a.code_dopp = s.code_dopp;
+  a.cls_fgroup = s.C ? s.cls_fgroup : nullptr;
+  a.cls_base = s.C ? s.cls_base : nullptr;
   return a;
 }
 
@@ -839,6 +852,8 @@ XcorrArgs xcorr_args(const AcqShape& s, const float2* d_Y, const float2* d_cspec
                      float* d_surface, RowStat* d_rows, unsigned* d_counters, gnss_detection* d_out) {
   XcorrArgs a;
   a.Y = d_Y;
+  a.bin_cls = s.C ? s.bin_cls : nullptr;
+  a.bin_shift = s.C ? s.bin_shift : nullptr;
   a.cspec = d_cspec;
   a.B = s.B;
   a.D = s.D;
@@ -936,7 +951,7 @@ AcqScratch scratch_layout(const AcqShape& s) {
   AcqScratch L;
   L.z = 0;
   L.y = L.z + al((size_t)s.G * s.B * s.N * sizeof(float2));
-  L.rows = L.y + al((size_t)s.D * s.B * s.N * sizeof(float2));
+  L.rows = L.y + al((size_t)(s.C ? s.C : s.D) * s.B * s.N * sizeof(float2));
   L.counters = L.rows + al((size_t)s.sets * s.P * s.D * sizeof(RowStat));
   L.total = L.counters + al((size_t)s.P * sizeof(unsigned));
   return L;

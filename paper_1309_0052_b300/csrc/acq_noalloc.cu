@@ -102,10 +102,12 @@ extern "C" GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void
   s.second_whole = (plan->desc.flags & GNSS_SECOND_WHOLE) ? 1 : 0;
   s.code_dopp = (plan->desc.flags & GNSS_CODE_DOPPLER) ? 1 : 0;
   s.threshold = plan->desc.threshold;
+  spectrum_args(plan, &s);
   const AcqScratch lay = scratch_layout(s);
   if (lay.total > GNSS_NOALLOC_SCRATCH_BYTES) {
     set_error("gnss_acquire_noalloc: this request needs " + std::to_string(lay.total) +
-              " bytes of scratch (folded blocks, n_dopp * blocks * N * 8 bytes of spectra, row statistics),"
+              " bytes of scratch (folded blocks, blocks * N * 8 bytes of spectra per class of bins a whole kHz apart"
+              " or per bin with code-Doppler compensation, row statistics),"
               " more than the fixed " + std::to_string((size_t)GNSS_NOALLOC_SCRATCH_BYTES) + " bytes");
     return GNSS_EINVAL;
   }

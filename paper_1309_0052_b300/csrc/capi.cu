@@ -101,6 +101,7 @@ static AcqShape shape_of(const gnss_plan* plan, int B) {
   s.second_whole = (plan->desc.flags & GNSS_SECOND_WHOLE) ? 1 : 0;
   s.code_dopp = (plan->desc.flags & GNSS_CODE_DOPPLER) ? 1 : 0;
   s.threshold = plan->desc.threshold;
+  spectrum_args(plan, &s);
   return s;
 }
 
@@ -171,6 +172,48 @@ static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_s
 
 namespace gnss {
 
+// Spectrum classes: bins whose frequencies differ by whole kHz have forward
+// spectra that are circular shifts of one another (a kHz is one cycle per
+// 1 ms block, one bin of its FFT), so each class keeps one spectrum per
+// block, the one of its lowest frequency, and bin d reads it shifted by
+// (f_d - base) / 1000.  A class spans under 16 kHz (shift < 16), which keeps
+// the shift below the correlate kernel's thread count.  The class's fold group is its bins' (fold groups
+// partition by f mod 1000 too, or hold every bin when coh_ms = 1).
+int spectrum_classes(const gnss_plan_desc& d, const std::vector<int>& group, std::vector<int>& packed) {
+  const int D = (int)d.n_dopp;
+  std::vector<int> key_of_class, fgroup, base, cls(D), shift(D);
+  for (int k = 0; k < D; ++k) {
+    const int64_t f = (int64_t)d.dopp_min_hz + (int64_t)k * d.dopp_step_hz;
+    const int key = (int)(((f % 1000) + 1000) % 1000);
+    int c = -1;  // the class of this residue whose base is within 15 kHz below f
+    for (size_t q = 0; q < key_of_class.size(); ++q)
+      if (key_of_class[q] == key && f - base[q] < 16 * 1000) c = (int)q;
+    if (c < 0) {  // bins ascend in frequency, so the first bin of a class is its lowest
+      c = (int)key_of_class.size();
+      key_of_class.push_back(key);
+      fgroup.push_back(group[k]);
+      base.push_back((int)f);
+    }
+    cls[k] = c;
+    shift[k] = (int)((f - base[c]) / 1000);
+  }
+  const int C = (int)key_of_class.size();
+  packed.clear();
+  packed.insert(packed.end(), fgroup.begin(), fgroup.end());
+  packed.insert(packed.end(), base.begin(), base.end());
+  packed.insert(packed.end(), cls.begin(), cls.end());
+  packed.insert(packed.end(), shift.begin(), shift.end());
+  return C;
+}
+
+void spectrum_args(const gnss_plan* plan, AcqShape* s) {
+  s->C = plan->C;
+  s->cls_fgroup = plan->C ? plan->d_cls : nullptr;
+  s->cls_base = plan->C ? plan->d_cls + plan->C : nullptr;
+  s->bin_cls = plan->C ? plan->d_cls + 2 * plan->C : nullptr;
+  s->bin_shift = plan->C ? plan->d_cls + 2 * plan->C + plan->D : nullptr;
+}
+
 // Fold groups: the per-millisecond wipe-off factor exp(-j 2 pi (f i mod 1000) / 1000)
 // depends on f only through f mod 1000 (and not at all with one coherent ms).
 int fold_groups(const gnss_plan_desc& d, std::vector<int>& group, std::vector<int>& gkey) {
@@ -228,8 +271,11 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   p->excl = (N + 1022) / 1023;
   for (int prn = 1; prn <= 32; ++prn)
     if (d.prn_mask >> (prn - 1) & 1ull) p->prns[p->P++] = prn;
-  std::vector<int> group, gkey;
+  std::vector<int> group, gkey, cls;
   p->G = fold_groups(d, group, gkey);
+  // shared spectra unless code-Doppler rotations make every bin's spectrum its own
+  p->C = (d.flags & GNSS_CODE_DOPPLER) ? 0 : spectrum_classes(d, group, cls);
+  if (p->C >= p->D) p->C = 0;  // nothing shared: keep one spectrum per bin
   cudaError_t e = cudaGetDevice(&p->device);
   cudaStream_t st = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
@@ -238,6 +284,7 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   if (e == cudaSuccess) e = cudaMalloc(&p->d_cspec, (size_t)p->P * N * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_group, sizeof(int) * p->D);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_gkey, sizeof(int) * p->G);
+  if (e == cudaSuccess && p->C) e = cudaMalloc(&p->d_cls, sizeof(int) * cls.size());
   int prn_index[33];
   for (int k = 0; k < 33; ++k) prn_index[k] = -1;
   for (int k = 0; k < p->P; ++k) prn_index[p->prns[k]] = k;
@@ -246,6 +293,8 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_prns, p->prns, sizeof(int) * p->P, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_group, group.data(), sizeof(int) * p->D, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_gkey, gkey.data(), sizeof(int) * p->G, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && p->C)
+    e = cudaMemcpyAsync(p->d_cls, cls.data(), sizeof(int) * cls.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_gold(p->d_prns, p->P, p->d_codes, st);
   if (e == cudaSuccess) e = launch_code_spectra(p->d_codes, p->P, N, p->d_cspec, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -258,6 +307,7 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
     cudaFree(p->d_cspec);
     cudaFree(p->d_group);
     cudaFree(p->d_gkey);
+    cudaFree(p->d_cls);
     cudaFree(p->d_prn_index);
     delete p;
     return r;
@@ -273,6 +323,7 @@ gnss_status gnss_plan_destroy(gnss_plan* plan) {
   cudaFree(plan->d_cspec);
   cudaFree(plan->d_group);
   cudaFree(plan->d_gkey);
+  cudaFree(plan->d_cls);
   cudaFree(plan->d_prn_index);
   delete plan;
   return GNSS_OK;
@@ -325,7 +376,8 @@ gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_dev, size_t
   if ((uintptr_t)samples_dev & 15u) return fail(GNSS_EINVAL, "device samples must be 16-byte aligned");
   const size_t L = (size_t)plan->desc.coh_ms * plan->N;
   if (n_blocks < 1 || (size_t)n_blocks > n_samples / L) return fail(GNSS_EINVAL, "n_blocks out of range");
-  const AcqShape s = shape_of(plan, (int)n_blocks);
+  AcqShape s = shape_of(plan, (int)n_blocks);
+  s.C = 0;  // the stage layout is one spectrum per bin
   const AcqScratch lay = scratch_layout(s);
   cudaStream_t cs = (cudaStream_t)stream;
   float2* d_Z = nullptr;
@@ -347,7 +399,8 @@ gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint
   if (st != GNSS_OK) return st;
   if ((plan->desc.flags & GNSS_SECOND_WHOLE) && !surface_dev)
     return fail(GNSS_EINVAL, "GNSS_SECOND_WHOLE needs a surface buffer");
-  const AcqShape s = shape_of(plan, (int)n_blocks);
+  AcqShape s = shape_of(plan, (int)n_blocks);
+  s.C = 0;  // the stage layout is one spectrum per bin
   const AcqScratch lay = scratch_layout(s);
   cudaStream_t cs = (cudaStream_t)stream;
   char* ws = nullptr;
@@ -426,7 +479,7 @@ gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t sc
         hr[k].car = carrier_args(sh, r.plan->d_group, Z, Y);
         hr[k].xc = xcorr_args(sh, Y, r.plan->d_cspec, r.plan->d_prns, r.surface_dev, rows, cnt, r.out_dev);
         const uint64_t nf = (uint64_t)fb[k] + (uint64_t)sh.G * sh.B * cpb;
-        const uint64_t nc = (uint64_t)cb[k] + (uint64_t)sh.D * sh.B;
+        const uint64_t nc = (uint64_t)cb[k] + (uint64_t)(sh.C ? sh.C : sh.D) * sh.B;  // carrier tiles
         const uint64_t nx = (uint64_t)xb[k] + (uint64_t)sh.P * sh.D;
         if (nf > INT32_MAX || nc > INT32_MAX || nx > INT32_MAX) too_many = true;
         fb[k + 1] = (uint32_t)nf;

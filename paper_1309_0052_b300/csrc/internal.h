@@ -38,11 +38,21 @@ struct AcqShape {
   int code_dopp;   // GNSS_CODE_DOPPLER
   int second_whole;
   float threshold;
+  // Spectrum classes: bins whose frequencies differ by whole kHz share one
+  // forward spectrum, circularly shifted (Y_{f + 1000 K}[k] = Y_f[k + K]).
+  // C = 0: one spectrum per bin (the stage entry points, code Doppler).
+  int C;                  // classes
+  const int* cls_fgroup;  // [C] fold group of each class
+  const int* cls_base;    // [C] frequency (Hz) of each class's spectrum
+  const int* bin_cls;     // [D] class of each bin
+  const int* bin_shift;   // [D] (f_d - cls_base) / 1000
 };
 
 // Kernel arguments of the correlate + detection kernel.
 struct XcorrArgs {
-  const float2* Y;        // [D][B][N] spectra of the wiped, folded blocks
+  const float2* Y;        // [D or C][B][N] spectra of the wiped, folded blocks
+  const int* bin_cls;     // NULL (row d of Y) or [D] spectrum row of each bin
+  const int* bin_shift;   // NULL or [D] circular shift of that row (bins)
   const float2* cspec;    // [P][N] code spectra
   int B, D, P, excl;
   float* surface;         // NULL or [sets][P][D][N]
@@ -68,7 +78,9 @@ struct FoldArgs {
 struct CarrierArgs {
   const float2* Z;         // [G][B][N]
   const int* group;        // [D] fold group per Doppler bin
-  float2* Y;               // [D][B][N]
+  const int* cls_fgroup;   // NULL (one spectrum per bin) or [C] fold group per class
+  const int* cls_base;     // [C] frequency of each class (with cls_fgroup)
+  float2* Y;               // [D or C][B][N]
   int fs, coh, B, dopp_min, dopp_step;
   int code_dopp;           // GNSS_CODE_DOPPLER: rotate block b by sigma_b samples
 };
@@ -154,6 +166,14 @@ gnss_status scratch_alloc(int dev, size_t bytes, cudaStream_t stream, void** out
 // Fold groups of a plan's Doppler grid (bins sharing f mod 1000; one group
 // when coh_ms == 1): group[d] for every bin, gkey[g] = f mod 1000.  Returns G.
 int fold_groups(const gnss_plan_desc& d, std::vector<int>& group, std::vector<int>& gkey);
+// Spectrum classes of a plan's grid (bins with equal f mod 1000): packed as
+// fold group [C], base frequency [C], class [D], shift [D].  Returns C.
+int spectrum_classes(const gnss_plan_desc& d, const std::vector<int>& group, std::vector<int>& packed);
+}  // namespace gnss
+struct gnss_plan;
+namespace gnss {
+// Set the spectrum-class fields of a shape from its plan.
+void spectrum_args(const gnss_plan* plan, AcqShape* s);
 
 // Last-error message (thread-local), set by the C-ABI layer.
 void set_error(const std::string& msg);
@@ -174,6 +194,8 @@ struct gnss_plan {
   int* d_group;       // [D] fold group of each Doppler bin
   int* d_gkey;        // [G] f mod 1000 of each group (0 when coh_ms == 1)
   int* d_prn_index;   // [33] plan index of PRN 1..32, -1 when not searched
+  int C;              // spectrum classes (0 with GNSS_CODE_DOPPLER: one per bin)
+  int* d_cls;         // [2 C + 2 D]: fold group [C], base Hz [C], class [D], shift [D]
   int8_t* d_codes;    // [P][1023] +-1 chips
   float2* d_cspec;    // [P][N] FFT of the sampled replica
 };

@@ -169,6 +169,7 @@ size_t device_need(const gnss_plan* plan, size_t n_samples) {
   s.B = (int)B;
   s.D = plan->D;
   s.G = plan->G;
+  s.C = plan->C;  // shared spectra (0: one per bin, the upper bound)
   s.P = plan->P;
   s.sets = plan->sets;
   return al256(rec_bytes_of(plan->desc.format, n_samples)) + al256(sizeof(gnss_detection) * plan->P) +
@@ -463,7 +464,7 @@ gnss_status gnss_submit(gnss_server* srv, const gnss_plan_desc* desc, const void
   if (!srv || !desc || !host_samples || !ticket) return fail_status(GNSS_EINVAL, "NULL argument");
   if (desc->flags & GNSS_SECOND_WHOLE) return fail_status(GNSS_EINVAL, "GNSS_SECOND_WHOLE needs surfaces; not served");
   if (desc->fs_hz == 0 || desc->fs_hz % 1000 || !supported_fft_size((int)(desc->fs_hz / 1000)) || desc->coh_ms < 1 ||
-      desc->n_dopp < 1 || desc->format > GNSS_FMT_2BIT_IQ || (desc->prn_mask & 0xFFFFFFFFull) == 0 ||
+      desc->n_dopp < 1 || desc->n_dopp > 100000 || desc->format > GNSS_FMT_2BIT_IQ || (desc->prn_mask & 0xFFFFFFFFull) == 0 ||
       (desc->prn_mask >> 32))
     return fail_status(GNSS_EINVAL, "invalid descriptor");
   const size_t N = desc->fs_hz / 1000;
@@ -475,7 +476,10 @@ gnss_status gnss_submit(gnss_server* srv, const gnss_plan_desc* desc, const void
     probe.desc = *desc;
     probe.N = (int)N;
     probe.D = (int)desc->n_dopp;
-    probe.G = desc->coh_ms == 1 ? 1 : (int)(desc->n_dopp < 1000 ? desc->n_dopp : 1000);
+    std::vector<int> group, gkey, cls;
+    probe.G = fold_groups(*desc, group, gkey);  // the plan's own fold groups and spectrum classes
+    probe.C = (desc->flags & GNSS_CODE_DOPPLER) ? 0 : spectrum_classes(*desc, group, cls);
+    if (probe.C >= probe.D) probe.C = 0;
     probe.P = __builtin_popcountll(desc->prn_mask);
     probe.sets = (desc->flags & GNSS_HALF_BIT) ? 2 : 1;
     if (device_need(&probe, n_samples) > srv->cfg.device_mem_budget)

@@ -63,7 +63,9 @@ def test_results_in_the_mix_equal_results_alone(g, recs, alone):
 
 
 def test_admission_by_device_memory(g, recs, alone):
-    budget = 400 << 20
+    # each of these requests holds at most ~20 MB in flight (folded blocks and
+    # the spectra shared by bins a whole kHz apart), the 14 together ~150 MB
+    budget = 40 << 20
     srv = g.Server(device_mem_budget=budget, max_batch=64)
     tickets = [srv.submit(g.Server.desc_for(r), r.raw, r.n_samples) for r in recs]
     seen = 0
@@ -81,7 +83,9 @@ def test_admission_by_device_memory(g, recs, alone):
 
 
 def test_request_larger_than_budget_is_refused(g, recs):
-    srv = g.Server(device_mem_budget=8 << 20)
+    # the 100 ms request holds about 3 MB in flight (recording, 1.3 MB of
+    # folded blocks, 1.3 MB of shared spectra, row statistics)
+    srv = g.Server(device_mem_budget=1 << 20)
     with pytest.raises(g.GnssError) as e:
         srv.submit(g.Server.desc_for(recs[-1]), recs[-1].raw, recs[-1].n_samples)
     assert e.value.status == g.EBUSY

@@ -57,8 +57,10 @@ def test_noalloc_matches_pool_path_on_consecutive_calls(g):
 
 def test_noalloc_rejects_requests_over_its_scratch(g):
     rec = siggen.weak_100ms()
-    plan = g.Plan.for_recording(rec)
-    n = 2 * rec.n_samples  # 20 blocks x 81 bins x 4096 x 8 B = 53 MB of spectra > 32 MiB
+    # with code-Doppler compensation every bin keeps its own spectra:
+    # 20 blocks x 81 bins x 4096 x 8 B = 53 MB > 32 MiB
+    plan = g.Plan.for_recording(rec, code_doppler=True)
+    n = 2 * rec.n_samples
     raw = torch.zeros(siggen.recording_bytes(n, rec.fmt), dtype=torch.uint8, device="cuda")
     out = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
     st = g.lib.gnss_acquire_noalloc(plan.handle, raw.data_ptr(), n, out.data_ptr(), None, None)
