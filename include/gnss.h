@@ -204,6 +204,19 @@ GNSS_API gnss_status gnss_acquire(gnss_plan* plan, const void* samples, size_t n
 GNSS_API gnss_status gnss_acquire_device(gnss_plan* plan, const void* samples_dev, size_t n_samples,
                                 gnss_detection* out_dev, float* surface_dev, void* stream);
 
+/* gnss_acquire_device with stage timing (a tracing aid: the paper profiles
+ * its GPU path as a timeline of short bursts, Section 5, Fig. 12).  events
+ * holds four caller-owned CUDA events (cudaEvent_t passed as void*, created
+ * with timing enabled; a NULL entry is skipped) that the call records on
+ * 'stream': [0] before the unpack/fold launch, [1] before the carrier +
+ * forward FFT launch, [2] before the correlate launch, [3] after it, so
+ * cudaEventElapsedTime of (2, 3) is the device time of the correlate stage
+ * of this very acquisition.  Same arithmetic, outputs and errors as
+ * gnss_acquire_device; GNSS_EINVAL if events is NULL. */
+GNSS_API gnss_status gnss_acquire_device_traced(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                       gnss_detection* out_dev, float* surface_dev, void* stream,
+                                       void* const* events);
+
 /* One request of a batched acquisition. */
 typedef struct {
   gnss_plan* plan;          /* plan of this request (fs, coherent length, Doppler grid, PRNs, format, flags) */
@@ -504,7 +517,11 @@ GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
  * 16 needs N <= 16384), and with 16 it can stage the
  * next block's spectrum into shared memory by a bulk TMA copy while the
  * current block is transformed (variant code 16 | GNSS_TUNE_STAGED, offered
- * where the CTA's shared memory still fits: N <= 8192).  With
+ * where the CTA's shared memory still fits: N <= 8192).  At N = 4096 the
+ * 16-per-thread form can also run the class-local pass schedule (variant
+ * code 16 | GNSS_TUNE_CLASS_LOCAL): after the first radix-16 pass the
+ * transform splits into 16 independent 256-point transforms, each on half a
+ * warp, so one CTA barrier per block instead of two.  With
  * force_elems = 0 every valid variant is timed on a probe shaped like the
  * plan (its Doppler bins up to 32, its sets, 8 blocks) and the fastest is
  * recorded for the plan's FFT size on the current device; with force_elems
@@ -512,12 +529,14 @@ GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
  * it is not valid for N).  Later launches of that FFT size (single, batched,
  * served) use it.  Synchronous.  out may be NULL. */
 #define GNSS_TUNE_STAGED 0x100u
+#define GNSS_TUNE_CLASS_LOCAL 0x200u
 typedef struct {
   uint32_t N;            /* FFT size tuned                                */
   uint32_t n_variants;   /* variants timed                                */
-  uint32_t elems[4];     /* variant code of each timed variant: elements  */
-                         /* per thread, | GNSS_TUNE_STAGED when staged    */
-  float ms[4];           /* median probe time of each (ms)                */
+  uint32_t elems[8];     /* variant code of each timed variant: elements  */
+                         /* per thread | GNSS_TUNE_STAGED or              */
+                         /* GNSS_TUNE_CLASS_LOCAL                         */
+  float ms[8];           /* median probe time of each (ms)                */
   uint32_t chosen;       /* variant code now in use for N                 */
 } gnss_tune_result;
 

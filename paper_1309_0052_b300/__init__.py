@@ -50,7 +50,7 @@ class ServerStats(C.Structure):
 
 
 class TuneResult(C.Structure):
-    _fields_ = [("N", C.c_uint32), ("n_variants", C.c_uint32), ("elems", C.c_uint32 * 4), ("ms", C.c_float * 4),
+    _fields_ = [("N", C.c_uint32), ("n_variants", C.c_uint32), ("elems", C.c_uint32 * 8), ("ms", C.c_float * 8),
                 ("chosen", C.c_uint32)]
 
 
@@ -91,6 +91,7 @@ _SIGS = {
     "gnss_recording_bytes": ([C.c_uint32, C.c_size_t], C.c_size_t),
     "gnss_acquire": ([_P, _P, C.c_size_t, C.c_int, _P, _P, _P], _st),
     "gnss_acquire_device": ([_P, _P, C.c_size_t, _P, _P, _P], _st),
+    "gnss_acquire_device_traced": ([_P, _P, C.c_size_t, _P, _P, _P, C.POINTER(_P)], _st),
     "gnss_acquire_noalloc": ([_P, _P, C.c_size_t, _P, _P, _P], _st),
     "gnss_stage_wipe_fft": ([_P, _P, C.c_size_t, C.c_uint32, _P, _P], _st),
     "gnss_stage_correlate": ([_P, _P, C.c_uint32, _P, _P, _P], _st),
@@ -265,6 +266,21 @@ class Plan:
         """gnss_acquire_device: out_dev is a CUDA uint8 tensor of n_prn * 28 bytes."""
         check(load().gnss_acquire_device(self._h, _ptr(samples_dev), n_samples, _ptr(out_dev), _ptr(surface),
                                       _stream_ptr(stream)), "gnss_acquire_device")
+
+    def acquire_device_traced(self, samples_dev, n_samples: int, out_dev, events, surface=None,
+                              stream=None) -> None:
+        """gnss_acquire_device_traced: events are four torch.cuda.Event
+        (enable_timing=True) recorded at the stage boundaries (before the fold,
+        before the carrier FFT, before and after the correlate launch)."""
+        import torch
+        handles = (_P * 4)()
+        for k, ev in enumerate(events):
+            if ev is not None and not ev.cuda_event:  # torch creates the event on its first record
+                ev.record(stream if stream is not None else torch.cuda.current_stream())
+            handles[k] = ev.cuda_event if ev is not None else None
+        check(load().gnss_acquire_device_traced(self._h, _ptr(samples_dev), n_samples, _ptr(out_dev),
+                                             _ptr(surface), _stream_ptr(stream), handles),
+              "gnss_acquire_device_traced")
 
     def stage_wipe_fft(self, samples_dev, n_samples: int, n_blocks: int, spectra_dev, stream=None) -> None:
         check(load().gnss_stage_wipe_fft(self._h, _ptr(samples_dev), n_samples, n_blocks, _ptr(spectra_dev),

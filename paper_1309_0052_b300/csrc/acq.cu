@@ -20,6 +20,20 @@
 namespace gnss {
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The carrier-FFT and correlate kernels are
+// launched so that their CTAs may start while the kernel before them on the
+// stream is still draining (launch latency and prologue overlap its tail);
+// each waits for that kernel's completion and memory (griddep_wait) before
+// it reads the kernel's output or writes anything.  The kernels before them
+// allow this early launch as soon as they start (griddep_release): the
+// dependent grid is scheduled only once every CTA of the primary has started,
+// and it waits for all of them to finish.  Without the launch attribute the
+// wait returns at once.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // K1: Gold codes.  Two-tap G2 phase selector per PRN (IS-GPS-200 Table 3-Ia).
 // Register bit s-1 holds stage s; the output is stage 10.
 // ---------------------------------------------------------------------------
@@ -66,13 +80,17 @@ struct Cfg {
 // Launch configuration of the correlate kernel with E elements per thread
 // (a tuning choice: 16 or 32, see xcorr_variant).  With ST the next block's
 // spectrum is staged into shared memory by a bulk TMA copy (N * 8 bytes more).
-template <int N, int E, bool ST = false>
+// With CL the transform runs the class-local schedule (N = 4096, E = 16, one
+// CTA barrier per block; fft4096_class_local).
+template <int N, int E, bool ST = false, bool CL = false>
 struct XCfg {
+  static_assert(!CL || (N == 4096 && E == 16 && !ST), "class-local schedule: N = 4096, 16 per thread");
   static constexpr int T = N / E;
   static constexpr bool TWC = (E <= 16);                        // twiddle bases cached in registers
-  static constexpr size_t buf_bytes = sizeof(float2) * FftShape<N>::smem_elems;
+  static constexpr size_t buf_bytes =
+      sizeof(float2) * (CL ? ClassLocal4096::smem_elems : FftShape<N>::smem_elems);
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
-  static constexpr size_t stage_off = (DB ? 2 : 1) * buf_bytes;
+  static constexpr size_t stage_off = (DB || CL ? 2 : 1) * buf_bytes;
   static constexpr size_t smem = stage_off + (ST ? sizeof(float2) * N : 0);
   // two CTAs per SM: up to 128 registers at 256 threads, 64 at 512 (E = 8)
   static constexpr int MINB = (T <= 256 || (E <= 8 && T <= 512)) ? 2 : 1;
@@ -128,8 +146,10 @@ __device__ __forceinline__ void load_ms(const uint8_t* __restrict__ base, int64_
   if constexpr (FMT == GNSS_FMT_2BIT_IQ) {
     // E samples = E/2 bytes; sample e: bits [4e, 4e+4) of the little-endian words
     const uint32_t* w = reinterpret_cast<const uint32_t*>(base + n0 / 2);
-    uint32_t words[E / 8];
-    if constexpr (E == 8) {
+    uint32_t words[E >= 8 ? E / 8 : 1];
+    if constexpr (E == 4) {
+      words[0] = __ldg(reinterpret_cast<const uint16_t*>(w));
+    } else if constexpr (E == 8) {
       words[0] = __ldg(w);
     } else if constexpr (E == 16) {
       const uint2 t = __ldg(reinterpret_cast<const uint2*>(w));
@@ -149,6 +169,16 @@ __device__ __forceinline__ void load_ms(const uint8_t* __restrict__ base, int64_
       // code c in 0..3 -> float c exactly via the 2^23 mantissa trick
       xi[e] = __int_as_float(0x4B000000 | ((word >> sh) & 3u)) - 8388608.f;
       xq[e] = __int_as_float(0x4B000000 | ((word >> (sh + 2)) & 3u)) - 8388608.f;
+    }
+  } else if constexpr (E == 4) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const int8_t*>(base) + 2 * n0));
+    const uint32_t wv[2] = {t.x, t.y};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      xi[2 * k] = (float)(int8_t)(wv[k] & 0xFF);
+      xq[2 * k] = (float)(int8_t)((wv[k] >> 8) & 0xFF);
+      xi[2 * k + 1] = (float)(int8_t)((wv[k] >> 16) & 0xFF);
+      xq[2 * k + 1] = (float)(int8_t)((wv[k] >> 24) & 0xFF);
     }
   } else {
     const int8_t* s = reinterpret_cast<const int8_t*>(base) + 2 * n0;
@@ -171,13 +201,14 @@ __device__ __forceinline__ void load_ms(const uint8_t* __restrict__ base, int64_
 // k_fold: z_g[m] = sum_i x[bL + iN + m] w_i for every fold group g and block b,
 // with w_i = exp(-j 2 pi ((rho_g i) mod 1000) / 1000), rho_g = f mod 1000 of
 // the Doppler bins of the group (all bins share one group when T_coh = 1).
-// Each thread folds 8 consecutive samples (one 4-byte load of 2-bit data or
-// one 16-byte load of int8 per millisecond); FoldCfg<N>::CPB CTAs of
+// Each thread folds 4 consecutive samples (one 2-byte load of 2-bit data or
+// one 8-byte load of int8 per millisecond: short per-thread chains, many
+// warps, since the fold is latency-bound); FoldCfg<N>::CPB CTAs of
 // FoldCfg<N>::T threads cover one (g, b).  Output in natural order.  CTA 0
 // also clears the per-PRN completion counters of k_xcorr.
 template <int N>
 struct FoldCfg {
-  static constexpr int E = 8;
+  static constexpr int E = 4;
   static constexpr int T = N / E < 128 ? N / E : 128;
   static constexpr int CPB = N / (E * T);  // CTAs per (group, block)
 };
@@ -187,6 +218,7 @@ __device__ __forceinline__ void fold_tile(const FoldArgs& a, int tile) {
   constexpr int E = FoldCfg<N>::E, T = FoldCfg<N>::T, CPB = FoldCfg<N>::CPB;
   const uint8_t* __restrict__ samples = a.samples;
   const int coh = a.coh, B = a.B;
+  griddep_release();
   const int gb = tile / CPB;             // g * B + b
   const int m0 = E * ((tile % CPB) * T + threadIdx.x);
   const int g = gb / B, b = gb % B;
@@ -198,7 +230,7 @@ __device__ __forceinline__ void fold_tile(const FoldArgs& a, int tile) {
 #pragma unroll
   for (int e = 0; e < E; ++e) ar[e] = ai[e] = 0.f;
   float wsum_r = 0.f, wsum_i = 0.f;
-#pragma unroll 5
+#pragma unroll 10
   for (int i = 0; i < coh; ++i) {
     const int ri = (int)(((int64_t)rho * i) % 1000);
     float ws, wc;
@@ -279,6 +311,7 @@ __device__ __forceinline__ int64_t code_doppler_sigma(int f, int b, int64_t L) {
 template <int N>
 __device__ __forceinline__ void carrier_tile(const CarrierArgs& a, int tile, float2* sm) {
   constexpr int E = Cfg<N>::E, T = Cfg<N>::T;
+  griddep_release();
   float2* buf0 = sm;
   float2* buf1 = Cfg<N>::DB ? sm + FftShape<N>::smem_elems : sm;
   const int fs = a.fs, coh = a.coh, B = a.B;
@@ -297,6 +330,7 @@ __device__ __forceinline__ void carrier_tile(const CarrierArgs& a, int tile, flo
   sincospif(-2.f * (float)rs * inv_fs, &ss, &sc);
   float2 car = make_float2(c0, s0);
   const float2 step = make_float2(sc, ss);
+  griddep_wait();  // the fold kernel's blocks are complete and visible
   float2 v[E];
   if (sh == 0) {  // uniform over the CTA
 #pragma unroll
@@ -495,7 +529,7 @@ struct StageIssue {
 // Y is read from L2; with staging it is read from the shared-memory stage
 // (once the stage's barrier phase has completed) and the copy of the next
 // block is issued after the IFFT's first barrier.
-template <int N, int E, bool DB, bool TWC, bool ST>
+template <int N, int E, bool DB, bool TWC, bool ST, bool CL>
 __device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh, const float2* __restrict__ cp,
                                            int j, float2* buf0, float2* buf1, int& phase, FftTw<N, E, true>& tw,
                                            float (&acc)[E], const StageIssue& next, uint32_t& parity,
@@ -525,8 +559,16 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh
     for (int r = 0; r < E - 1; ++r) v[r] = c_mulconj(__ldcg(ys + T * r), __ldg(cp + j + T * r));
     const int last = js + T * (E - 1);
     v[E - 1] = c_mulconj(__ldcg(y + (last >= N ? last - N : last)), __ldg(cp + j + T * (E - 1)));
-    if constexpr (TWC) fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw);
-    else fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
+    if constexpr (CL) {
+      // one buffer per block, alternating: the next block's first-pass stores
+      // go to the other buffer, so no barrier guards this block's last reads
+      fft4096_class_local<true>(v, j, phase ? buf1 : buf0, tw);
+      phase ^= 1;
+    } else if constexpr (TWC) {
+      fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw);
+    } else {
+      fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
+    }
   }
 #pragma unroll
   for (int r = 0; r < E; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
@@ -587,21 +629,23 @@ __device__ __forceinline__ void finalize_prn(const XcorrArgs& a, int p, int sets
   if (threadIdx.x == 0) a.out[p] = rec;
 }
 
-template <int N, int E, bool HALF, bool ST>
+template <int N, int E, bool HALF, bool ST, bool CL>
 __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2* sm) {
-  using X = XCfg<N, E, ST>;
+  using X = XCfg<N, E, ST, CL>;
   constexpr int T = X::T;
   constexpr bool DB = X::DB, TWC = X::TWC;
   constexpr int S = HALF ? 2 : 1;
   static_assert(!ST || TWC, "staging is built with cached twiddles");
   float2* buf0 = sm;
-  float2* buf1 = DB ? sm + FftShape<N>::smem_elems : sm;
+  float2* buf1 = (DB || CL) ? sm + X::buf_bytes / sizeof(float2) : sm;
   __shared__ float s_val[32];
   __shared__ uint32_t s_idx[32];
   __shared__ unsigned s_last;
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ int s_stage_fail;
   const int j = threadIdx.x;
+  // thread j ends each transform holding |R|^2 of phases jo + T r
+  const int jo = CL ? ClassLocal4096::perm(j) : j;
   const int p = tile % a.P, d = tile / a.P;
   const float2* cp = a.cspec + (size_t)p * N;
   // bin d's spectrum: its own row, or its class's row read K bins further
@@ -612,6 +656,9 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
                   (uint32_t)(sizeof(float2) * N), j};
   uint32_t parity = 0;
   bool stage_ok = true;
+  FftTw<N, E, true> tw;
+  if constexpr (TWC) tw.init(jo);  // the first pass has no twiddles; later passes run butterfly jo
+  griddep_wait();  // the spectra and the cleared counters are complete and visible
   if constexpr (ST) {
     if (j == 0) {
       s_stage_fail = 0;
@@ -620,8 +667,6 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
     __syncthreads();
     if (j == 0) stage_issue(next.stg, yd, next.bytes, &s_mbar);  // block 0 of set 0
   }
-  FftTw<N, E, true> tw;
-  if constexpr (TWC) tw.init(j);
   int phase = 0;
 #pragma unroll 1
   for (int set = 0; set < S; ++set) {
@@ -635,8 +680,8 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
         if (nb >= a.B) nb = set + 1 < S ? set + 1 : a.B;
         next.src = nb < a.B ? yd + (size_t)nb * N : nullptr;
       }
-      corr_block<N, E, DB, TWC, ST>(yd + (size_t)b * N, ksh, cp, j, buf0, buf1, phase, tw, acc, next, parity,
-                                    stage_ok);
+      corr_block<N, E, DB, TWC, ST, CL>(yd + (size_t)b * N, ksh, cp, j, buf0, buf1, phase, tw, acc, next,
+                                        parity, stage_ok);
     }
     // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
     constexpr float sc = 1.f / ((float)N * (float)N);
@@ -645,9 +690,9 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
     if (a.surface != nullptr) {
       float* row = a.surface + (((size_t)set * a.P + p) * a.D + d) * (size_t)N;
 #pragma unroll
-      for (int r = 0; r < E; ++r) row[j + T * r] = acc[r];
+      for (int r = 0; r < E; ++r) row[jo + T * r] = acc[r];
     }
-    row_stats<N, E>(acc, j, a.excl, s_val, s_idx, a.rows + ((size_t)set * a.P + p) * a.D + d);
+    row_stats<N, E>(acc, jo, a.excl, s_val, s_idx, a.rows + ((size_t)set * a.P + p) * a.D + d);
   }
   if constexpr (ST) {
     // A wait that gave up may leave a copy in flight: wait for it once more
@@ -659,29 +704,49 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
       stage_wait(&s_mbar, parity ^ 1u);
     }
   }
-  // The last CTA of PRN p (of its D Doppler rows) runs the detection.
-  __threadfence();
+  // The last CTA of PRN p (of its D Doppler rows) runs the detection.  The
+  // CTA barrier orders every row and surface write of this CTA before thread
+  // 0's fence and count (release); the CTA that counts last fences before
+  // reading the other CTAs' rows (acquire).
   __syncthreads();
-  if (j == 0) s_last = (atomicAdd(a.counters + p, 1u) == (unsigned)(a.D - 1)) ? 1u : 0u;
-  __syncthreads();
-  if (s_last) {
+  if (a.second_whole) {
+    // the whole-surface second peak scans D N cells per set: all threads
+    if (j == 0) {
+      __threadfence();
+      s_last = (atomicAdd(a.counters + p, 1u) == (unsigned)(a.D - 1)) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      finalize_prn<N, T>(a, p, S, s_val, s_idx);
+    }
+    return;
+  }
+  // otherwise warp 0 alone counts and detects; the other warps leave now
+  if (j >= 32) return;
+  unsigned last = 0;
+  if (j == 0) {
     __threadfence();
-    finalize_prn<N, T>(a, p, S, s_val, s_idx);
+    last = (atomicAdd(a.counters + p, 1u) == (unsigned)(a.D - 1)) ? 1u : 0u;
+  }
+  if (__shfl_sync(0xffffffffu, last, 0)) {
+    __threadfence();
+    finalize_prn<N, 32>(a, p, S, s_val, s_idx);
   }
 }
 
-template <int N, int E, bool HALF, bool ST>
-__global__ void __launch_bounds__(XCfg<N, E>::T, XCfg<N, E>::MINB) k_xcorr(const XcorrArgs a) {
+template <int N, int E, bool HALF, bool ST, bool CL>
+__global__ void __launch_bounds__(XCfg<N, E, ST, CL>::T, XCfg<N, E, ST, CL>::MINB) k_xcorr(const XcorrArgs a) {
   extern __shared__ __align__(16) float2 sm[];
-  xcorr_tile<N, E, HALF, ST>(a, blockIdx.x, sm);
+  xcorr_tile<N, E, HALF, ST, CL>(a, blockIdx.x, sm);
 }
 
-template <int N, int E, bool HALF, bool ST>
-__global__ void __launch_bounds__(XCfg<N, E>::T, XCfg<N, E>::MINB)
+template <int N, int E, bool HALF, bool ST, bool CL>
+__global__ void __launch_bounds__(XCfg<N, E, ST, CL>::T, XCfg<N, E, ST, CL>::MINB)
     k_xcorr_batch(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ base, int n) {
   extern __shared__ __align__(16) float2 sm[];
   const int r = find_request(base, n);
-  xcorr_tile<N, E, HALF, ST>(reqs[r].xc, (int)(blockIdx.x - __ldg(base + r)), sm);
+  xcorr_tile<N, E, HALF, ST, CL>(reqs[r].xc, (int)(blockIdx.x - __ldg(base + r)), sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -694,6 +759,23 @@ bool supported_fft_size(int N) {
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Launch with programmatic stream serialization (see griddep_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                                   cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 cudaError_t launch_gold(const int* d_prns, int P, int8_t* d_codes, cudaStream_t stream) {
@@ -727,7 +809,8 @@ cudaError_t launch_code_spectra(const int8_t* d_codes, int P, int N, float2* d_c
 
 template <int N>
 static cudaError_t wipe_fft_n(const AcqShape& s, const uint8_t* d_samples, const int* d_group, const int* d_gkey,
-                              float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream) {
+                              float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream,
+                              cudaEvent_t between) {
   const int fgrid = s.G * s.B * FoldCfg<N>::CPB;
   const FoldArgs fa = fold_args(s, d_samples, d_gkey, d_Z, d_counters);
   if (s.format == GNSS_FMT_2BIT_IQ)
@@ -736,22 +819,28 @@ static cudaError_t wipe_fft_n(const AcqShape& s, const uint8_t* d_samples, const
     k_fold<N, GNSS_FMT_I8_IQ><<<fgrid, FoldCfg<N>::T, 0, stream>>>(fa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (between && (e = cudaEventRecord(between, stream)) != cudaSuccess) return e;
   e = set_smem(k_carrier_fft<N>, Cfg<N>::smem);
   if (e != cudaSuccess) return e;
-  k_carrier_fft<N><<<(s.C ? s.C : s.D) * s.B, Cfg<N>::T, Cfg<N>::smem, stream>>>(carrier_args(s, d_group, d_Z, d_Y));
-  return cudaGetLastError();
+  return launch_dependent(k_carrier_fft<N>, (s.C ? s.C : s.D) * s.B, Cfg<N>::T, Cfg<N>::smem, stream,
+                          carrier_args(s, d_group, d_Z, d_Y));
 }
 
 cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const int* d_group, const int* d_gkey,
-                            float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream) {
-  GNSS_DISPATCH_N(s.N, return wipe_fft_n<NN>(s, d_samples, d_group, d_gkey, d_Z, d_Y, d_counters, stream));
+                            float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream,
+                            cudaEvent_t between) {
+  GNSS_DISPATCH_N(s.N, return wipe_fft_n<NN>(s, d_samples, d_group, d_gkey, d_Z, d_Y, d_counters, stream,
+                                             between));
 }
 
 // Correlate-kernel variant per device and FFT size: elements per thread E,
 // plus GNSS_TUNE_STAGED for the TMA-staged form.
 static int g_xcorr_e[128][15];
 
-int xcorr_default_e(int N) { return N >= 16384 ? 32 : 16; }
+int xcorr_default_e(int N) {
+  if (N == 4096) return 16 | (int)GNSS_TUNE_CLASS_LOCAL;
+  return N >= 16384 ? 32 : 16;
+}
 
 static bool stage_fits(int N) {
   switch (N) {
@@ -768,6 +857,7 @@ static bool stage_fits(int N) {
 
 bool xcorr_valid_e(int N, int code) {
   if (code == (16 | (int)GNSS_TUNE_STAGED)) return N / 16 <= 1024 && stage_fits(N);
+  if (code == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return N == 4096;
   return (code == 16 && N / 16 <= 1024) || (code == 32 && N >= 1024) || (code == 8 && N / 8 <= 1024);
 }
 
@@ -788,20 +878,19 @@ void set_xcorr_variant(int N, int E) {
   if (dev >= 0 && dev < 128 && lg < 15) __atomic_store_n(&g_xcorr_e[dev][lg], E, __ATOMIC_RELAXED);
 }
 
-template <int N, int E, bool ST>
+template <int N, int E, bool ST, bool CL = false>
 static cudaError_t xcorr_ne(const AcqShape& s, const XcorrArgs& a, cudaStream_t stream) {
-  using X = XCfg<N, E, ST>;
+  using X = XCfg<N, E, ST, CL>;
   const int grid = s.P * s.D;
   if (s.sets == 2) {
-    cudaError_t e = set_smem(k_xcorr<N, E, true, ST>, X::smem);
+    cudaError_t e = set_smem(k_xcorr<N, E, true, ST, CL>, X::smem);
     if (e != cudaSuccess) return e;
-    k_xcorr<N, E, true, ST><<<grid, X::T, X::smem, stream>>>(a);
+    return launch_dependent(k_xcorr<N, E, true, ST, CL>, grid, X::T, X::smem, stream, a);
   } else {
-    cudaError_t e = set_smem(k_xcorr<N, E, false, ST>, X::smem);
+    cudaError_t e = set_smem(k_xcorr<N, E, false, ST, CL>, X::smem);
     if (e != cudaSuccess) return e;
-    k_xcorr<N, E, false, ST><<<grid, X::T, X::smem, stream>>>(a);
+    return launch_dependent(k_xcorr<N, E, false, ST, CL>, grid, X::T, X::smem, stream, a);
   }
-  return cudaGetLastError();
 }
 
 template <int N>
@@ -815,6 +904,9 @@ static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t s
   }
   if constexpr (StageFits<N>::value) {
     if (v == (16 | (int)GNSS_TUNE_STAGED)) return xcorr_ne<N, 16, true>(s, a, stream);
+  }
+  if constexpr (N == 4096) {
+    if (v == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return xcorr_ne<N, 16, false, true>(s, a, stream);
   }
   return xcorr_ne<N, 16, false>(s, a, stream);
 }
@@ -878,18 +970,19 @@ cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_c
   GNSS_DISPATCH_N(s.N, return xcorr_n<NN>(s, a, stream));
 }
 
-template <int N, int E, bool ST>
+template <int N, int E, bool ST, bool CL = false>
 static cudaError_t xcorr_batch_ne(const BatchGroup& g, cudaStream_t stream) {
-  using X = XCfg<N, E, ST>;
+  using X = XCfg<N, E, ST, CL>;
   cudaError_t e;
   if (g.sets == 2) {
-    if ((e = set_smem(k_xcorr_batch<N, E, true, ST>, X::smem)) != cudaSuccess) return e;
-    k_xcorr_batch<N, E, true, ST><<<g.xc_ctas, X::T, X::smem, stream>>>(g.reqs, g.xc_base, g.n);
+    if ((e = set_smem(k_xcorr_batch<N, E, true, ST, CL>, X::smem)) != cudaSuccess) return e;
+    return launch_dependent(k_xcorr_batch<N, E, true, ST, CL>, g.xc_ctas, X::T, X::smem, stream, g.reqs, g.xc_base,
+                            g.n);
   } else {
-    if ((e = set_smem(k_xcorr_batch<N, E, false, ST>, X::smem)) != cudaSuccess) return e;
-    k_xcorr_batch<N, E, false, ST><<<g.xc_ctas, X::T, X::smem, stream>>>(g.reqs, g.xc_base, g.n);
+    if ((e = set_smem(k_xcorr_batch<N, E, false, ST, CL>, X::smem)) != cudaSuccess) return e;
+    return launch_dependent(k_xcorr_batch<N, E, false, ST, CL>, g.xc_ctas, X::T, X::smem, stream, g.reqs,
+                            g.xc_base, g.n);
   }
-  return cudaGetLastError();
 }
 
 // Batched launches: every request of the group shares N, format and sets.
@@ -902,8 +995,9 @@ static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
     k_fold_batch<N, GNSS_FMT_I8_IQ><<<g.fold_ctas, FoldCfg<N>::T, 0, stream>>>(g.reqs, g.fold_base, g.n);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = set_smem(k_carrier_fft_batch<N>, Cfg<N>::smem)) != cudaSuccess) return e;
-  k_carrier_fft_batch<N><<<g.car_ctas, Cfg<N>::T, Cfg<N>::smem, stream>>>(g.reqs, g.car_base, g.n);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_dependent(k_carrier_fft_batch<N>, g.car_ctas, Cfg<N>::T, Cfg<N>::smem, stream, g.reqs, g.car_base,
+                            g.n)) != cudaSuccess)
+    return e;
   const int v = xcorr_variant(N);
   if constexpr (N >= 1024) {
     if (v == 32) return xcorr_batch_ne<N, 32, false>(g, stream);
@@ -913,6 +1007,9 @@ static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
   }
   if constexpr (StageFits<N>::value) {
     if (v == (16 | (int)GNSS_TUNE_STAGED)) return xcorr_batch_ne<N, 16, true>(g, stream);
+  }
+  if constexpr (N == 4096) {
+    if (v == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return xcorr_batch_ne<N, 16, false, true>(g, stream);
   }
   return xcorr_batch_ne<N, 16, false>(g, stream);
 }

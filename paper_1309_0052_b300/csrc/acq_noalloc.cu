@@ -19,8 +19,9 @@
 #include "internal.h"
 
 // Fixed scratch shared by every gnss_acquire_noalloc call on a device.
-// 32 MiB holds the spectra of the 100 ms / 4.096 MHz / 81-bin / 10-block
-// workload (26.5 MB) plus its row statistics.
+// 32 MiB holds the scratch of the 100 ms / 4.096 MHz / 81-bin / 10-block
+// workload: 2.6 MB of spectra per class of bins (26.5 MB per bin with code
+// Doppler) plus its folded blocks and row statistics.
 #define GNSS_NOALLOC_SCRATCH_BYTES (32u << 20)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GNSS_NOALLOC_SCRATCH_BYTES];
 

@@ -120,7 +120,7 @@ static size_t rec_bytes(uint32_t format, size_t n) {
 // Shared body of gnss_acquire / gnss_acquire_device.
 static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_samples, int samples_on_device,
                                 gnss_detection* out_host, gnss_detection* out_dev, float* surface_dev,
-                                cudaStream_t stream) {
+                                cudaStream_t stream, void* const* events = nullptr) {
   if (!plan || !samples || (!out_host && !out_dev)) return fail(GNSS_EINVAL, "NULL argument");
   gnss_status st = check_plan_device(plan);
   if (st != GNSS_OK) return st;
@@ -149,9 +149,18 @@ static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_s
                         cudaMemcpyHostToDevice, stream);
     d_smp = dst;
   }
-  if (e == cudaSuccess) e = launch_wipe_fft(s, d_smp, plan->d_group, plan->d_gkey, d_Z, d_Y, d_cnt, stream);
+  // stage-boundary events of the traced entry point (caller-owned)
+  auto mark = [&](int k) {
+    if (e == cudaSuccess && events && events[k]) e = cudaEventRecord((cudaEvent_t)events[k], stream);
+  };
+  mark(0);
+  if (e == cudaSuccess)
+    e = launch_wipe_fft(s, d_smp, plan->d_group, plan->d_gkey, d_Z, d_Y, d_cnt, stream,
+                        events ? (cudaEvent_t)events[1] : nullptr);
+  mark(2);
   if (e == cudaSuccess)
     e = launch_xcorr(s, d_Y, plan->d_cspec, plan->d_prns, surface_dev, d_rows, d_cnt, d_det, stream);
+  mark(3);
   if (e == cudaSuccess && out_host)
     e = cudaMemcpyAsync(out_host, d_det, (size_t)s.P * sizeof(gnss_detection), cudaMemcpyDeviceToHost, stream);
   cudaError_t ef = cudaFreeAsync(ws, stream);
@@ -366,6 +375,14 @@ gnss_status gnss_acquire_device(gnss_plan* plan, const void* samples_dev, size_t
                                 gnss_detection* out_dev, float* surface_dev, void* stream) {
   if (!out_dev) return fail(GNSS_EINVAL, "NULL argument");
   return acquire_impl(plan, samples_dev, n_samples, 1, nullptr, out_dev, surface_dev, (cudaStream_t)stream);
+}
+
+gnss_status gnss_acquire_device_traced(gnss_plan* plan, const void* samples_dev, size_t n_samples,
+                                       gnss_detection* out_dev, float* surface_dev, void* stream,
+                                       void* const* events) {
+  if (!out_dev || !events) return fail(GNSS_EINVAL, "NULL argument");
+  return acquire_impl(plan, samples_dev, n_samples, 1, nullptr, out_dev, surface_dev, (cudaStream_t)stream,
+                      events);
 }
 
 gnss_status gnss_stage_wipe_fft(gnss_plan* plan, const void* samples_dev, size_t n_samples, uint32_t n_blocks,

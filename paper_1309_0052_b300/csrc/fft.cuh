@@ -495,3 +495,70 @@ __device__ __forceinline__ void fft_block_tw(float2 (&v)[E], int j, float2* buf0
 }
 
 }  // namespace gnss
+
+namespace gnss {
+
+// ---------------------------------------------------------------------------
+// Class-local schedule of the 4096-point transform (16 elements per thread,
+// 256 threads): one CTA-wide exchange per transform instead of two.
+//
+// The first radix-16 pass (inputs at stride 256, straight from registers)
+// writes its output digit c into slot i with i mod 16 = c.  Every later
+// Stockham pass reads x[J + 256 s] and writes y[(J / NS) 16 NS + k + t NS]
+// with NS a multiple of 16, so it maps slots of one residue class c = J mod
+// 16 onto the same class: the rest of the transform is 16 independent
+// 256-point transforms, one per class.  Butterfly J of those passes runs on
+// thread t = 16 (J mod 16) + J / 16, so class c lives on the 16 lanes
+// 16c .. 16c + 15 (half a warp); after the CTA barrier of the first exchange
+// the second exchange needs only __syncwarp, in place in the same buffer
+// (each half-warp reads its class's slots, then overwrites exactly them).
+// On exit thread t holds X[jp + 256 r] in v[r], jp = (t >> 4) + 16 (t & 15).
+//
+// Shared-memory slot of element i: i + i/16 + i/256.  Lanes of a half-warp
+// then hit distinct bank pairs in all four access patterns (first-pass
+// stores at 16 t + u, class gathers at jp + 256 r, second-pass stores at
+// 256 (jp / 16) + jp mod 16 + 16 u), and every access is a per-thread base
+// plus a compile-time offset.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pad_cl(int i) { return i + (i >> 4) + (i >> 8); }
+
+struct ClassLocal4096 {
+  static constexpr int N = 4096, E = 16, T = 256;
+  static constexpr int smem_elems = N + N / 16 + N / 256;  // > pad_cl(N - 1)
+  // thread of butterfly J in the class passes (an involution on [0, 256))
+  __device__ __forceinline__ static int perm(int t) { return (t >> 4) + 16 * (t & 15); }
+};
+
+template <bool INV, typename Hook = NoHook>
+__device__ __forceinline__ void fft4096_class_local(float2 (&v)[16], int t, float2* __restrict__ buf,
+                                                    const FftTw<4096, 16, INV>& tw, const Hook& hook = Hook()) {
+  // pass 1 (NS = 1): DFT16 over stride 256; outputs to 16 t + u
+  pass_compute_tw<4096, 16, 16, 1, INV>(v, tw);
+  {
+    float2* b = buf + pad_cl(16 * t);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[u] = v[u];
+  }
+  __syncthreads();
+  hook();
+  const int jp = ClassLocal4096::perm(t);
+  const float2* g = buf + pad_cl(jp);  // element jp + 256 r sits at g[273 r]
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = g[273 * r];
+  // pass 2 (NS = 16), butterfly jp: twiddles of k = jp mod 16
+  pass_compute_tw<4096, 16, 16, 16, INV>(v, tw.next);
+  __syncwarp();  // the half-warp has read every slot of its class
+  {
+    // output u of butterfly jp goes to 256 (jp / 16) + jp mod 16 + 16 u
+    float2* b = buf + pad_cl(256 * (jp >> 4) + (jp & 15));
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[17 * u] = v[u];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = g[273 * r];
+  // pass 3 (NS = 256), butterfly jp: twiddles of k = jp
+  pass_compute_tw<4096, 16, 16, 256, INV>(v, tw.next.next);
+}
+
+}  // namespace gnss

@@ -125,8 +125,11 @@ cudaError_t launch_gold(const int* d_prns, int P, int8_t* d_codes, cudaStream_t 
 cudaError_t launch_code_spectra(const int8_t* d_codes, int P, int N, float2* d_cspec, cudaStream_t stream);
 // k_fold + k_carrier_fft: Y from the recording.  d_counters (may be NULL) is
 // cleared for the k_xcorr launch that follows on the same stream.
+// fold, then carrier + forward FFT; 'between' (may be NULL) is recorded on
+// the stream between the two launches.
 cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const int* d_group, const int* d_gkey,
-                            float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream);
+                            float2* d_Z, float2* d_Y, unsigned* d_counters, cudaStream_t stream,
+                            cudaEvent_t between = nullptr);
 // k_xcorr: surfaces, row statistics and per-PRN detections.  d_counters must
 // be zero on entry.
 cudaError_t launch_xcorr(const AcqShape& s, const float2* d_Y, const float2* d_cspec, const int* d_prns,

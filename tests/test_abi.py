@@ -105,6 +105,8 @@ def test_host_side_rejections_of_later_entry_points(lib):
     fn = L.gnss_acquire_noalloc
     fn.argtypes = [C.c_void_p] * 3 + [C.c_void_p] * 3
     assert fn(None, None, 0, None, None, None) == E
+    # traced acquisition: NULL events or outputs are rejected before any device work
+    assert L.gnss_acquire_device_traced(None, None, 0, None, None, None, None) == E
     cfg = lib.TrackConfig(1, 10, 1.0, 15.0, 1.0, 0)
     assert L.gnss_track(None, None, 0, None, 1, C.byref(cfg), None, None) == E
 

@@ -137,6 +137,28 @@ def test_host_device_and_async_paths_agree(g):
     np.testing.assert_array_equal(det_async, det_dev)
 
 
+def test_traced_acquisition_same_records_and_ordered_events(g):
+    """The traced entry point gives the untraced records and surfaces, and its
+    four stage events are recorded in order on the launching stream."""
+    rec = siggen.weak_100ms()
+    plan = g.Plan.for_recording(rec)
+    raw = _dev(rec.raw)
+    s = torch.cuda.Stream()
+    o1 = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+    o2 = torch.zeros_like(o1)
+    s1 = torch.zeros(plan.surface_shape(), dtype=torch.float32, device="cuda")
+    s2 = torch.zeros_like(s1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    plan.acquire_device(raw, rec.n_samples, o1, surface=s1, stream=s)
+    plan.acquire_device_traced(raw, rec.n_samples, o2, ev, surface=s2, stream=s)
+    s.synchronize()
+    np.testing.assert_array_equal(o1.cpu().numpy(), o2.cpu().numpy())
+    np.testing.assert_array_equal(s1.cpu().numpy(), s2.cpu().numpy())
+    gaps = [ev[k].elapsed_time(ev[k + 1]) for k in range(3)]
+    assert all(t > 0 for t in gaps), gaps
+    assert gaps[2] > gaps[0] and gaps[2] > gaps[1]  # the correlate stage dominates
+
+
 @pytest.mark.parametrize("extra,noncoh", [(0.5, 0), (0.0, 2), (2.7, 3)])
 def test_ragged_tail_and_noncoh_cap(g, extra, noncoh):
     rec = siggen.plain_4ms()

@@ -32,6 +32,7 @@ def _recording(N, coh, B, fmt, seed):
 
 
 STAGED = 0x100
+CLASS_LOCAL = 0x200
 
 
 def _valid(N):
@@ -42,6 +43,8 @@ def _valid(N):
         v.append(16 | STAGED)
     if N <= 8192:
         v.append(8)
+    if N == 4096:
+        v.append(16 | CLASS_LOCAL)
     return v
 
 
@@ -56,7 +59,7 @@ def test_every_shape_matches_oracle(g, N, half, B):
     x = oracle.unpack(raw, n, fmt)
     S = oracle.surfaces(x, N * 1000, coh, B, half, prns, dopp[0] + dopp[1] * np.arange(dopp[2]), 8)
     ref = oracle.detect(S, prns)
-    default = 32 if N >= 16384 else 16
+    default = 32 if N >= 16384 else (16 | CLASS_LOCAL) if N == 4096 else 16
     try:
         for elems in _valid(N):
             assert plan.autotune(elems)["chosen"] == elems
@@ -80,6 +83,9 @@ def test_invalid_shape_rejected(g):
     big = g.Plan(16_384_000, 1, 0, 1, 1, prns=[1])
     with pytest.raises(g.GnssError) as e:
         big.autotune(16 | STAGED)  # the stage does not fit beside the 16384-point exchange buffer
+    assert e.value.status == g.EINVAL
+    with pytest.raises(g.GnssError) as e:
+        big.autotune(16 | CLASS_LOCAL)  # the class-local schedule is built for N = 4096 only
     assert e.value.status == g.EINVAL
 
 
@@ -111,7 +117,7 @@ def test_staged_full_size_and_batch(g):
             items.append((p, rr, r.n_samples, out, sf))
         g.acquire_batch(items)
         torch.cuda.synchronize()
-        plan.autotune(16)
+        plan.autotune(16 | CLASS_LOCAL)  # the default at N = 4096
         for p, rr, n, out, sf in items:
             o2 = torch.zeros_like(out)
             s2 = torch.zeros_like(sf)
@@ -125,4 +131,27 @@ def test_staged_full_size_and_batch(g):
             A, Bs = sf.cpu().numpy(), s2.cpu().numpy()
             assert np.abs(A - Bs).max() <= 1e-6 * np.abs(Bs).max()
     finally:
-        plan.autotune(16)
+        plan.autotune(16 | CLASS_LOCAL)
+
+
+def test_class_local_matches_two_barrier_schedule(g):
+    """The class-local schedule (the default at N = 4096) runs the same
+    butterflies with the same operands as the two-barrier schedule, only on
+    other threads, so on the full 100 ms workload both give identical
+    surfaces and records."""
+    rec = siggen.weak_100ms()
+    plan = g.Plan.for_recording(rec)
+    raw = torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda()
+    res = {}
+    try:
+        for code in (16, 16 | CLASS_LOCAL):
+            plan.autotune(code)
+            surf = torch.zeros(plan.surface_shape(), dtype=torch.float32, device="cuda")
+            det = plan.acquire(raw, rec.n_samples, surface=surf)
+            res[code] = (det, surf.cpu().numpy())
+    finally:
+        plan.autotune(16 | CLASS_LOCAL)
+    (d0, s0), (d1, s1) = res[16], res[16 | CLASS_LOCAL]
+    np.testing.assert_array_equal(s0, s1)
+    for f in ("prn", "detected", "set", "dopp_bin", "code_phase", "peak", "second", "ratio"):
+        np.testing.assert_array_equal(d0[f], d1[f])
