@@ -431,26 +431,54 @@ __device__ __forceinline__ float block_max(float v, float* s_val) {
   return v;
 }
 
+template <int T>
+__device__ __forceinline__ uint32_t block_min_u32(uint32_t v, uint32_t* s_idx) {
+  constexpr int W = (T + 31) / 32;
+#pragma unroll
+  for (int o = WarpShape<T>::first; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(WarpShape<T>::mask, v, o));
+  if constexpr (W > 1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) s_idx[warp] = v;
+    __syncthreads();
+    v = s_idx[0];
+#pragma unroll
+    for (int w = 1; w < W; ++w) v = min(v, s_idx[w]);
+  }
+  return v;
+}
+
+// Row statistics of one (PRN, Doppler) row held as a[r] = S[j + T r]:
+// peak = max S, tau = the smallest phase holding it, second = max S over the
+// phases whose circular distance to tau exceeds excl (0 if none).  Only the
+// threads whose own maximum is the peak search their phases for it, and only
+// the threads holding a phase inside the band (with 2 excl + 1 <= T at most
+// one per thread, the phases of a thread being T apart) scan their cells for
+// the second peak; every other thread's contribution is its own maximum.
 template <int N, int E>
 __device__ __forceinline__ void row_stats(const float (&a)[E], int j, int excl, float* s_val, uint32_t* s_idx,
                                           RowStat* out) {
   constexpr int T = N / E;
-  float best = -1.f;
-  uint32_t bt = 0;
+  float tmax = a[0];
 #pragma unroll
-  for (int r = 0; r < E; ++r) {  // ascending r = ascending code phase for this thread
-    if (a[r] > best) {
-      best = a[r];
-      bt = (uint32_t)(j + T * r);
-    }
+  for (int r = 1; r < E; ++r) tmax = fmaxf(tmax, a[r]);
+  const float best = block_max<T>(tmax, s_val);
+  uint32_t bt = 0xffffffffu;
+  if (tmax == best) {
+#pragma unroll
+    for (int r = E - 1; r >= 0; --r)
+      if (a[r] == best) bt = (uint32_t)(j + T * r);
   }
-  block_argmax<T>(best, bt, s_val, s_idx);
-  float sec = 0.f;  // every cell is >= 0
+  bt = block_min_u32<T>(bt, s_idx);
+  float sec = tmax;
+  if (2 * excl + 1 > T || ((j - (int)bt + excl) & (T - 1)) <= 2 * excl) {
+    sec = 0.f;  // every cell is >= 0
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    int dist = abs(j + T * r - (int)bt);
-    dist = min(dist, N - dist);
-    if (dist > excl) sec = fmaxf(sec, a[r]);
+    for (int r = 0; r < E; ++r) {
+      int dist = abs(j + T * r - (int)bt);
+      dist = min(dist, N - dist);
+      if (dist > excl) sec = fmaxf(sec, a[r]);
+    }
   }
   sec = block_max<T>(sec, s_val);
   if (threadIdx.x == 0) {

@@ -25,8 +25,13 @@
 
 namespace gnss {
 
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sums and differences as two-wide FP32 operations (fadd.f32x2 /
+// fma.f32x2: one instruction for both components; per component the same
+// round-to-nearest result as the scalar form, a - b being fma(b, -1, a)).
+// Complex products stay scalar: their packed form needs swapped operands and
+// broadcast twiddle pairs, which cost more registers than the kernels have.
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -134,7 +139,7 @@ __device__ __forceinline__ float2 c_fma(float2 a, float2 w, float2 b) {
 }
 // 2 a - t (the other output of a butterfly whose first output t = a + u).
 __device__ __forceinline__ float2 c_twice_minus(float2 a, float2 t) {
-  return make_float2(fmaf(2.f, a.x, -t.x), fmaf(2.f, a.y, -t.y));
+  return __ffma2_rn(make_float2(2.f, 2.f), a, make_float2(-t.x, -t.y));
 }
 
 // 4-point DFT of (x0, y x1, y^2 x2, y^3 x3) in place, given y1 = y and
