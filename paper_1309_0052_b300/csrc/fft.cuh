@@ -25,13 +25,13 @@
 
 namespace gnss {
 
-// Complex sums and differences as two-wide FP32 operations (fadd.f32x2 /
-// fma.f32x2: one instruction for both components; per component the same
-// round-to-nearest result as the scalar form, a - b being fma(b, -1, a)).
-// Complex products stay scalar: their packed form needs swapped operands and
-// broadcast twiddle pairs, which cost more registers than the kernels have.
+// Complex sums and differences as two-wide FP32 operations (add.f32x2: one
+// instruction for both components; per component the same round-to-nearest
+// result as the scalar form).  Complex products stay scalar: their packed
+// form needs swapped operands and broadcast twiddle pairs, which cost more
+// registers than the kernels have.
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
