@@ -14,6 +14,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fft.cuh"
 #include "internal.h"
 
@@ -213,32 +215,47 @@ struct FoldCfg {
   static constexpr int CPB = N / (E * T);  // CTAs per (group, block)
 };
 
-template <int N, int FMT>
-__device__ __forceinline__ void fold_tile(const FoldArgs& a, int tile) {
-  constexpr int E = FoldCfg<N>::E, T = FoldCfg<N>::T, CPB = FoldCfg<N>::CPB;
-  const uint8_t* __restrict__ samples = a.samples;
-  const int coh = a.coh, B = a.B;
-  griddep_release();
-  const int gb = tile / CPB;             // g * B + b
-  const int m0 = E * ((tile % CPB) * T + threadIdx.x);
-  const int g = gb / B, b = gb % B;
-  if (a.counters != nullptr && tile == 0)
-    for (int p = threadIdx.x; p < a.P; p += T) a.counters[p] = 0u;
-  const int rho = a.gkey[g];
-  const int64_t n_first = (int64_t)b * coh * N + m0;  // first sample of this thread, ms 0
-  float ar[E], ai[E];
+// exp(-j 2 pi k / 1000), k < 1000: the per-millisecond wipe-off factors
+// w_i = c_root1000[(rho i) mod 1000], computed in double on the host and
+// rounded once; every lane of a CTA reads the same entry (a broadcast).
+__constant__ float2 c_root1000[1000];
+
+cudaError_t ensure_fold_roots() {
+  static std::mutex mu;
+  static bool done[128];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return cudaSuccess;
+  float2 h[1000];
+  for (int k = 0; k < 1000; ++k) {
+    const double ang = 2.0 * M_PI * (double)k / 1000.0;
+    h[k] = make_float2((float)cos(ang), (float)-sin(ang));
+  }
+  e = cudaMemcpyToSymbol(c_root1000, h, sizeof(h));
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
+// Fold of E consecutive samples starting at n_first (ms 0 of the block) over
+// coh milliseconds: z[e] = sum_i x[n_first + i N + e] w_i.  For 2-bit data
+// x = 2c - 3(1 + j): fold 2c w, then subtract 3(1 + j) sum(w).
+template <int N, int E, int FMT>
+__device__ __forceinline__ void fold_samples(const uint8_t* __restrict__ samples, int64_t n_first, int coh, int rho,
+                                             float (&ar)[E], float (&ai)[E]) {
 #pragma unroll
   for (int e = 0; e < E; ++e) ar[e] = ai[e] = 0.f;
   float wsum_r = 0.f, wsum_i = 0.f;
 #pragma unroll 10
   for (int i = 0; i < coh; ++i) {
-    const int ri = (int)(((int64_t)rho * i) % 1000);
-    float ws, wc;
-    sincospif(-2.f * (float)ri / 1000.f, &ws, &wc);
+    const float2 w = c_root1000[(int)(((int64_t)rho * i) % 1000)];
+    const float ws = w.y, wc = w.x;
     float xi[E], xq[E];
     load_ms<E, FMT>(samples, n_first + (int64_t)i * N, xi, xq);
     float wr = wc, wi = ws;
-    if constexpr (FMT == GNSS_FMT_2BIT_IQ) {  // x = 2c - 3(1 + j): fold 2c w here, -3(1 + j) sum(w) after
+    if constexpr (FMT == GNSS_FMT_2BIT_IQ) {
       wr *= 2.f;
       wi *= 2.f;
       wsum_r += wc;
@@ -259,6 +276,20 @@ __device__ __forceinline__ void fold_tile(const FoldArgs& a, int tile) {
       ai[e] = fmaf(-3.f, wsum_r + wsum_i, ai[e]);
     }
   }
+}
+
+template <int N, int FMT>
+__device__ __forceinline__ void fold_tile(const FoldArgs& a, int tile) {
+  constexpr int E = FoldCfg<N>::E, T = FoldCfg<N>::T, CPB = FoldCfg<N>::CPB;
+  griddep_release();
+  const int B = a.B;
+  const int gb = tile / CPB;             // g * B + b
+  const int m0 = E * ((tile % CPB) * T + threadIdx.x);
+  const int g = gb / B, b = gb % B;
+  if (a.counters != nullptr && tile == 0)
+    for (int p = threadIdx.x; p < a.P; p += T) a.counters[p] = 0u;
+  float ar[E], ai[E];
+  fold_samples<N, E, FMT>(a.samples, (int64_t)b * a.coh * N + m0, a.coh, a.gkey[g], ar, ai);
   float4* out = reinterpret_cast<float4*>(a.Z + ((size_t)gb * N + m0));
 #pragma unroll
   for (int e = 0; e < E; e += 2) out[e / 2] = make_float4(ar[e], ai[e], ar[e + 1], ai[e + 1]);

@@ -286,6 +286,7 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   p->C = (d.flags & GNSS_CODE_DOPPLER) ? 0 : spectrum_classes(d, group, cls);
   if (p->C >= p->D) p->C = 0;  // nothing shared: keep one spectrum per bin
   cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = ensure_fold_roots();
   cudaStream_t st = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_prns, sizeof(int) * p->P);

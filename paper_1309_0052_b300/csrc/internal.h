@@ -125,6 +125,9 @@ cudaError_t launch_gold(const int* d_prns, int P, int8_t* d_codes, cudaStream_t 
 cudaError_t launch_code_spectra(const int8_t* d_codes, int P, int N, float2* d_cspec, cudaStream_t stream);
 // k_fold + k_carrier_fft: Y from the recording.  d_counters (may be NULL) is
 // cleared for the k_xcorr launch that follows on the same stream.
+// Upload the fold kernel's per-millisecond factors to the current device
+// (once per device; plan creation calls it).
+cudaError_t ensure_fold_roots();
 // fold, then carrier + forward FFT; 'between' (may be NULL) is recorded on
 // the stream between the two launches.
 cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const int* d_group, const int* d_gkey,
