@@ -189,8 +189,9 @@ def make_workloads(args):
 
 
 def run_batch(g, torch, batch, stream, flush, steps):
-    """256 uneven recordings: one gnss_acquire_batch per step vs one
-    gnss_acquire_device per recording, recordings resident on the device."""
+    """256 uneven recordings: one gnss_acquire_batch per step, one replay of
+    the same batch captured into a CUDA graph (gnss_batch_graph_*), and one
+    gnss_acquire_device per recording; recordings resident on the device."""
     plans = {}
     items = []
     for r in batch:
@@ -210,8 +211,13 @@ def run_batch(g, torch, batch, stream, flush, steps):
         for plan, raw, n, out, _ in items:
             plan.acquire_device(raw, n, out, stream=stream)
 
+    graph = g.BatchGraph(items)  # captured once, outside the timed region
+
+    def graph_replay():
+        graph.launch(stream=stream)
+
     res = {}
-    for name, fn in (("batched", batched), ("one_request_per_launch", per_request)):
+    for name, fn in (("batched", batched), ("graph", graph_replay), ("one_request_per_launch", per_request)):
         with torch.cuda.stream(stream):
             fn()
         torch.cuda.synchronize()
@@ -227,7 +233,9 @@ def run_batch(g, torch, batch, stream, flush, steps):
             ms.append(e0.elapsed_time(e1))
         t = statistics.median(ms)
         res[name] = {"ms_per_batch": t, "cells_per_s": cells / (t * 1e-3), "requests_per_s": len(items) / (t * 1e-3)}
+    graph.close()
     res["speedup"] = res["one_request_per_launch"]["ms_per_batch"] / res["batched"]["ms_per_batch"]
+    res["graph_speedup"] = res["one_request_per_launch"]["ms_per_batch"] / res["graph"]["ms_per_batch"]
     res["requests"] = len(items)
     res["cells_per_batch"] = cells
     res["workload"] = ("uneven recordings 20-200 ms, fs {2.048, 4.096, 8.192} MHz, 2-bit, 32 PRN, "

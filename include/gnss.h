@@ -239,6 +239,28 @@ typedef struct {
  * GNSS_ENOMEM, GNSS_ECUDA. */
 GNSS_API gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t scratch_budget, void* stream);
 
+/* The batch above captured once into a CUDA graph and replayed with one
+ * launch: the batch mode of Section 5 (one batched GPU call in place of many
+ * small ones, Listing 3b) for a service that refills fixed recording slots.
+ * gnss_batch_graph_create validates the requests exactly as
+ * gnss_acquire_batch does, allocates the graph's own scratch (one region of
+ * the largest wave's size, reused by the waves in order, plus the launch
+ * tables), writes the launch tables and captures every wave's launches;
+ * it is synchronous.  The requests' plans, sample, output and surface
+ * pointers are baked in: they must stay valid, and unchanged in size, while
+ * the graph lives; their contents may change between launches (a new
+ * recording in the same buffer gives that recording's results).
+ * gnss_batch_graph_launch enqueues one replay on 'stream' (asynchronous;
+ * outputs are valid once the stream has synchronised); replays on one stream
+ * run in order, replays that overlap on the GPU race on the graph's scratch.
+ * Errors: GNSS_EINVAL (NULL or empty, any invalid request, a graph of
+ * another device), GNSS_ENOMEM, GNSS_ECUDA. */
+typedef struct gnss_batch_graph gnss_batch_graph;
+GNSS_API gnss_status gnss_batch_graph_create(const gnss_request* reqs, size_t n_req, size_t scratch_budget,
+                                             gnss_batch_graph** out);
+GNSS_API gnss_status gnss_batch_graph_launch(gnss_batch_graph* graph, void* stream);
+GNSS_API gnss_status gnss_batch_graph_destroy(gnss_batch_graph* graph);
+
 /* Second-stage fine Doppler search around coarse detections.  For each of
  * the n_det host records in det (typically the detected ones of a
  * gnss_acquire on this plan and recording), the acquisition of Section 3,

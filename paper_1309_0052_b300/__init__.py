@@ -100,6 +100,9 @@ _SIGS = {
                     _st),
     "gnss_refine_device": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_double, _P, _P], _st),
     "gnss_acquire_batch": ([_P, C.c_size_t, C.c_size_t, _P], _st),
+    "gnss_batch_graph_create": ([_P, C.c_size_t, C.c_size_t, C.POINTER(_P)], _st),
+    "gnss_batch_graph_launch": ([_P, _P], _st),
+    "gnss_batch_graph_destroy": ([_P], _st),
     "gnss_acquire_zoom": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.c_uint32, C.c_uint32, _P, _P, _P], _st),
     "gnss_track": ([_P, _P, C.c_size_t, _P, C.c_size_t, C.POINTER(TrackConfig), _P, _P], _st),
     "gnss_server_create": ([_P, C.POINTER(_P)], _st),
@@ -354,6 +357,36 @@ def acquire_batch(requests, scratch_budget: int = 0, stream=None) -> None:
         arr[k] = Request(plan.handle.value if hasattr(plan.handle, "value") else plan.handle, _ptr(smp), n,
                          _ptr(out), _ptr(surf))
     check(load().gnss_acquire_batch(arr, len(reqs), scratch_budget, _stream_ptr(stream)), "gnss_acquire_batch")
+
+
+class BatchGraph:
+    """gnss_batch_graph_*: a batch of requests (as for acquire_batch) captured
+    once into a CUDA graph; launch() replays it.  The tensors of the requests
+    are kept referenced for the graph's life (their addresses are baked in)."""
+
+    def __init__(self, requests, scratch_budget: int = 0):
+        self._reqs = list(requests)
+        arr = (Request * len(self._reqs))()
+        for k, (plan, smp, n, out, surf) in enumerate(self._reqs):
+            arr[k] = Request(plan.handle.value if hasattr(plan.handle, "value") else plan.handle, _ptr(smp), n,
+                             _ptr(out), _ptr(surf))
+        self._h = C.c_void_p()
+        check(load().gnss_batch_graph_create(arr, len(self._reqs), scratch_budget, C.byref(self._h)),
+              "gnss_batch_graph_create")
+
+    def launch(self, stream=None) -> None:
+        check(load().gnss_batch_graph_launch(self._h, _stream_ptr(stream)), "gnss_batch_graph_launch")
+
+    def close(self) -> None:
+        if self._h:
+            load().gnss_batch_graph_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

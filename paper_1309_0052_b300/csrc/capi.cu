@@ -435,18 +435,31 @@ gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint
   return GNSS_OK;
 }
 
-gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t scratch_budget, void* stream) {
-  if (n_req == 0) return GNSS_OK;
+}  // extern "C"
+
+namespace gnss {
+
+// Batched acquisition, planned once on the host: requests are validated and
+// grouped by (FFT size, format, sets); each group runs longest first and is
+// cut into waves whose scratch fits the budget.  A wave's device tables are
+// its BatchReq records and the three CTA-offset arrays.
+struct Wave {
+  int N, format, sets;
+  std::vector<size_t> idx;  // requests of the wave, in launch order
+  size_t bytes;             // scratch of its requests
+};
+
+static size_t wave_desc_bytes(size_t n) {
+  return align256(sizeof(BatchReq) * n) + align256(3 * sizeof(uint32_t) * (n + 1));
+}
+
+static gnss_status plan_batch(const gnss_request* reqs, size_t n_req, size_t scratch_budget, int dev,
+                              std::vector<AcqShape>& shape, std::vector<AcqScratch>& lay, std::vector<Wave>& waves) {
   if (!reqs) return fail(GNSS_EINVAL, "NULL argument");
   if (n_req > (size_t)INT32_MAX) return fail(GNSS_EINVAL, "too many requests");
   if (scratch_budget == 0) scratch_budget = (size_t)16 << 30;
-  cudaStream_t cs = (cudaStream_t)stream;
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  // validate everything before launching anything
-  std::vector<AcqShape> shape(n_req);
-  std::vector<AcqScratch> lay(n_req);
+  shape.assign(n_req, AcqShape());
+  lay.assign(n_req, AcqScratch());
   std::map<std::tuple<int, int, int>, std::vector<size_t>> groups;
   for (size_t i = 0; i < n_req; ++i) {
     const gnss_request& r = reqs[i];
@@ -462,6 +475,7 @@ gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t sc
     lay[i] = scratch_layout(shape[i]);
     groups[std::make_tuple(shape[i].N, shape[i].format, shape[i].sets)].push_back(i);
   }
+  waves.clear();
   for (auto& kv : groups) {
     std::vector<size_t>& idx = kv.second;
     // longest correlate CTAs (most blocks) first, so the tail is short ones
@@ -470,70 +484,208 @@ gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t sc
     while (pos < idx.size()) {
       size_t end = pos, bytes = 0;
       while (end < idx.size() && (end == pos || bytes + lay[idx[end]].total <= scratch_budget)) bytes += lay[idx[end++]].total;
-      const int n = (int)(end - pos);
-      const size_t desc_bytes = align256(sizeof(BatchReq) * n) + align256(3 * sizeof(uint32_t) * (n + 1));
-      char* ws = nullptr;
-      gnss_status st = scratch_alloc(dev, desc_bytes + bytes, cs, (void**)&ws);
-      if (st != GNSS_OK) return st;
-      std::vector<BatchReq> hr(n);
-      std::vector<uint32_t> hb(3 * (size_t)(n + 1));
-      uint32_t* fb = hb.data();
-      uint32_t* cb = fb + (n + 1);
-      uint32_t* xb = cb + (n + 1);
-      fb[0] = cb[0] = xb[0] = 0;
-      char* cur = ws + desc_bytes;
-      const uint32_t cpb = fold_ctas_per_block(shape[idx[pos]].N);
-      bool too_many = false;
-      for (int k = 0; k < n; ++k) {
-        const size_t i = idx[pos + k];
-        const gnss_request& r = reqs[i];
+      Wave w;
+      w.N = std::get<0>(kv.first);
+      w.format = std::get<1>(kv.first);
+      w.sets = std::get<2>(kv.first);
+      w.idx.assign(idx.begin() + pos, idx.begin() + end);
+      w.bytes = bytes;
+      // CTA counts of the three launches must fit the 32-bit offsets
+      uint64_t nf = 0, nc = 0, nx = 0;
+      const uint32_t cpb = fold_ctas_per_block(w.N);
+      for (size_t i : w.idx) {
         const AcqShape& sh = shape[i];
-        const AcqScratch& L = lay[i];
-        float2* Z = reinterpret_cast<float2*>(cur + L.z);
-        float2* Y = reinterpret_cast<float2*>(cur + L.y);
-        RowStat* rows = reinterpret_cast<RowStat*>(cur + L.rows);
-        unsigned* cnt = reinterpret_cast<unsigned*>(cur + L.counters);
-        hr[k].fold = fold_args(sh, (const uint8_t*)r.samples_dev, r.plan->d_gkey, Z, cnt);
-        hr[k].car = carrier_args(sh, r.plan->d_group, Z, Y);
-        hr[k].xc = xcorr_args(sh, Y, r.plan->d_cspec, r.plan->d_prns, r.surface_dev, rows, cnt, r.out_dev);
-        const uint64_t nf = (uint64_t)fb[k] + (uint64_t)sh.G * sh.B * cpb;
-        const uint64_t nc = (uint64_t)cb[k] + (uint64_t)(sh.C ? sh.C : sh.D) * sh.B;  // carrier tiles
-        const uint64_t nx = (uint64_t)xb[k] + (uint64_t)sh.P * sh.D;
-        if (nf > INT32_MAX || nc > INT32_MAX || nx > INT32_MAX) too_many = true;
-        fb[k + 1] = (uint32_t)nf;
-        cb[k + 1] = (uint32_t)nc;
-        xb[k + 1] = (uint32_t)nx;
-        cur += L.total;
+        nf += (uint64_t)sh.G * sh.B * cpb;
+        nc += (uint64_t)(sh.C ? sh.C : sh.D) * sh.B;
+        nx += (uint64_t)sh.P * sh.D;
       }
-      if (too_many) {
-        cudaFreeAsync(ws, cs);
+      if (nf > INT32_MAX || nc > INT32_MAX || nx > INT32_MAX)
         return fail(GNSS_EINVAL, "a wave needs more than 2^31 CTAs; lower scratch_budget");
-      }
-      BatchReq* d_reqs = reinterpret_cast<BatchReq*>(ws);
-      uint32_t* d_base = reinterpret_cast<uint32_t*>(ws + align256(sizeof(BatchReq) * n));
-      e = cudaMemcpyAsync(d_reqs, hr.data(), sizeof(BatchReq) * n, cudaMemcpyHostToDevice, cs);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(d_base, hb.data(), sizeof(uint32_t) * hb.size(), cudaMemcpyHostToDevice, cs);
-      if (e == cudaSuccess) {
-        BatchGroup g;
-        g.N = std::get<0>(kv.first);
-        g.format = std::get<1>(kv.first);
-        g.sets = std::get<2>(kv.first);
-        g.n = n;
-        g.reqs = d_reqs;
-        g.fold_base = d_base;
-        g.car_base = d_base + (n + 1);
-        g.xc_base = d_base + 2 * (n + 1);
-        g.fold_ctas = fb[n];
-        g.car_ctas = cb[n];
-        g.xc_ctas = xb[n];
-        e = launch_batch(g, cs);
-      }
-      cudaError_t ef = cudaFreeAsync(ws, cs);
-      if (e != cudaSuccess) return cuda_fail(e, "gnss_acquire_batch");
-      if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+      waves.push_back(std::move(w));
       pos = end;
     }
   }
+  return GNSS_OK;
+}
+
+// Host tables of one wave whose request scratch starts at 'scratch' and whose
+// device tables will be copied to 'desc'; g describes the launch triple.
+static void fill_wave(const Wave& w, const gnss_request* reqs, const std::vector<AcqShape>& shape,
+                      const std::vector<AcqScratch>& lay, char* scratch, char* desc, std::vector<BatchReq>& hr,
+                      std::vector<uint32_t>& hb, BatchGroup& g) {
+  const int n = (int)w.idx.size();
+  hr.assign(n, BatchReq());
+  hb.assign(3 * (size_t)(n + 1), 0u);
+  uint32_t* fb = hb.data();
+  uint32_t* cb = fb + (n + 1);
+  uint32_t* xb = cb + (n + 1);
+  char* cur = scratch;
+  const uint32_t cpb = fold_ctas_per_block(w.N);
+  for (int k = 0; k < n; ++k) {
+    const size_t i = w.idx[k];
+    const gnss_request& r = reqs[i];
+    const AcqShape& sh = shape[i];
+    const AcqScratch& L = lay[i];
+    float2* Z = reinterpret_cast<float2*>(cur + L.z);
+    float2* Y = reinterpret_cast<float2*>(cur + L.y);
+    RowStat* rows = reinterpret_cast<RowStat*>(cur + L.rows);
+    unsigned* cnt = reinterpret_cast<unsigned*>(cur + L.counters);
+    hr[k].fold = fold_args(sh, (const uint8_t*)r.samples_dev, r.plan->d_gkey, Z, cnt);
+    hr[k].car = carrier_args(sh, r.plan->d_group, Z, Y);
+    hr[k].xc = xcorr_args(sh, Y, r.plan->d_cspec, r.plan->d_prns, r.surface_dev, rows, cnt, r.out_dev);
+    fb[k + 1] = fb[k] + (uint32_t)(sh.G * sh.B * cpb);
+    cb[k + 1] = cb[k] + (uint32_t)((sh.C ? sh.C : sh.D) * sh.B);  // carrier tiles
+    xb[k + 1] = xb[k] + (uint32_t)(sh.P * sh.D);
+    cur += L.total;
+  }
+  BatchReq* d_reqs = reinterpret_cast<BatchReq*>(desc);
+  uint32_t* d_base = reinterpret_cast<uint32_t*>(desc + align256(sizeof(BatchReq) * n));
+  g.N = w.N;
+  g.format = w.format;
+  g.sets = w.sets;
+  g.n = n;
+  g.reqs = d_reqs;
+  g.fold_base = d_base;
+  g.car_base = d_base + (n + 1);
+  g.xc_base = d_base + 2 * (n + 1);
+  g.fold_ctas = fb[n];
+  g.car_ctas = cb[n];
+  g.xc_ctas = xb[n];
+}
+
+}  // namespace gnss
+
+extern "C" {
+
+gnss_status gnss_acquire_batch(const gnss_request* reqs, size_t n_req, size_t scratch_budget, void* stream) {
+  if (n_req == 0) return GNSS_OK;
+  if (!reqs) return fail(GNSS_EINVAL, "NULL argument");
+  cudaStream_t cs = (cudaStream_t)stream;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  // validate everything before launching anything
+  std::vector<AcqShape> shape;
+  std::vector<AcqScratch> lay;
+  std::vector<Wave> waves;
+  gnss_status st = plan_batch(reqs, n_req, scratch_budget, dev, shape, lay, waves);
+  if (st != GNSS_OK) return st;
+  std::vector<BatchReq> hr;
+  std::vector<uint32_t> hb;
+  for (const Wave& w : waves) {
+    const size_t desc_bytes = wave_desc_bytes(w.idx.size());
+    char* ws = nullptr;
+    st = scratch_alloc(dev, desc_bytes + w.bytes, cs, (void**)&ws);
+    if (st != GNSS_OK) return st;
+    BatchGroup g;
+    fill_wave(w, reqs, shape, lay, ws + desc_bytes, ws, hr, hb, g);
+    e = cudaMemcpyAsync(ws, hr.data(), sizeof(BatchReq) * hr.size(), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<uint32_t*>(g.fold_base), hb.data(), sizeof(uint32_t) * hb.size(),
+                          cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = launch_batch(g, cs);
+    cudaError_t ef = cudaFreeAsync(ws, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "gnss_acquire_batch");
+    if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync");
+  }
+  return GNSS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched acquisition captured once into a CUDA graph (the batch mode of
+// Section 5 as one replayable launch).
+// ---------------------------------------------------------------------------
+struct gnss_batch_graph {
+  int device;
+  size_t n_req;
+  void* scratch;  // one region reused by every wave (waves run in order)
+  void* desc;     // every wave's device tables
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+gnss_status gnss_batch_graph_create(const gnss_request* reqs, size_t n_req, size_t scratch_budget,
+                                    gnss_batch_graph** out) {
+  if (!out) return fail(GNSS_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (n_req == 0) return fail(GNSS_EINVAL, "empty batch");
+  if (!reqs) return fail(GNSS_EINVAL, "NULL argument");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::vector<AcqShape> shape;
+  std::vector<AcqScratch> lay;
+  std::vector<Wave> waves;
+  gnss_status st = plan_batch(reqs, n_req, scratch_budget, dev, shape, lay, waves);
+  if (st != GNSS_OK) return st;
+  size_t scratch_bytes = 0, desc_bytes = 0;
+  for (const Wave& w : waves) {
+    scratch_bytes = std::max(scratch_bytes, w.bytes);
+    desc_bytes += wave_desc_bytes(w.idx.size());
+  }
+  gnss_batch_graph* g = new (std::nothrow) gnss_batch_graph();
+  if (!g) return fail(GNSS_ENOMEM, "host allocation failed");
+  g->device = dev;
+  g->n_req = n_req;
+  cudaStream_t cs = nullptr;
+  e = cudaMalloc(&g->scratch, scratch_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->desc, desc_bytes);
+  // device tables are written now; the graph holds only the launches
+  std::vector<BatchGroup> groups(waves.size());
+  std::vector<BatchReq> hr;
+  std::vector<uint32_t> hb;
+  size_t off = 0;
+  for (size_t k = 0; k < waves.size() && e == cudaSuccess; ++k) {
+    char* d = reinterpret_cast<char*>(g->desc) + off;
+    fill_wave(waves[k], reqs, shape, lay, reinterpret_cast<char*>(g->scratch), d, hr, hb, groups[k]);
+    e = cudaMemcpy(d, hr.data(), sizeof(BatchReq) * hr.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(const_cast<uint32_t*>(groups[k].fold_base), hb.data(), sizeof(uint32_t) * hb.size(),
+                     cudaMemcpyHostToDevice);
+    off += wave_desc_bytes(waves[k].idx.size());
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t el = cudaSuccess;
+    for (size_t k = 0; k < groups.size() && el == cudaSuccess; ++k) el = launch_batch(groups[k], cs);
+    e = cudaStreamEndCapture(cs, &g->graph);  // ends the capture even after a failed launch
+    if (e == cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    gnss_status r = (e == cudaErrorMemoryAllocation) ? fail(GNSS_ENOMEM, "device allocation failed")
+                                                      : cuda_fail(e, "gnss_batch_graph_create");
+    gnss_batch_graph_destroy(g);
+    return r;
+  }
+  *out = g;
+  return GNSS_OK;
+}
+
+gnss_status gnss_batch_graph_launch(gnss_batch_graph* g, void* stream) {
+  if (!g) return fail(GNSS_EINVAL, "NULL argument");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != g->device) return fail(GNSS_EINVAL, "graph belongs to another device than the current one");
+  e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gnss_batch_graph_launch");
+  return GNSS_OK;
+}
+
+gnss_status gnss_batch_graph_destroy(gnss_batch_graph* g) {
+  if (!g) return GNSS_OK;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  cudaFree(g->scratch);
+  cudaFree(g->desc);
+  delete g;
   return GNSS_OK;
 }
 

@@ -107,6 +107,12 @@ def test_host_side_rejections_of_later_entry_points(lib):
     assert fn(None, None, 0, None, None, None) == E
     # traced acquisition: NULL events or outputs are rejected before any device work
     assert L.gnss_acquire_device_traced(None, None, 0, None, None, None, None) == E
+    # batch graph: NULL handle slot, NULL graph; destroying NULL is a no-op
+    h = C.c_void_p()
+    assert L.gnss_batch_graph_create(None, 1, 0, None) == E
+    assert L.gnss_batch_graph_create(None, 0, 0, C.byref(h)) == E and not h.value
+    assert L.gnss_batch_graph_launch(None, None) == E
+    assert L.gnss_batch_graph_destroy(None) == lib.OK
     cfg = lib.TrackConfig(1, 10, 1.0, 15.0, 1.0, 0)
     assert L.gnss_track(None, None, 0, None, 1, C.byref(cfg), None, None) == E
 

@@ -91,3 +91,65 @@ def test_batch_rejects_invalid_request_before_launching(g, mix):
     assert e.value.status == g.EINVAL
     assert b"request 1" in g.lib.gnss_last_error()
     g.acquire_batch([])  # empty batch is a no-op
+
+
+@pytest.mark.parametrize("budget", [0, 200 << 20])
+def test_batch_graph_replays_the_batch(g, mix, budget):
+    """The batch captured into a CUDA graph: each replay gives exactly the
+    records and surfaces of gnss_acquire_batch, with one wave per group or
+    several waves sharing the graph's scratch; two replays in a row on one
+    stream give the same results again."""
+    ref_outs, ref_surfs = _batched(g, mix, budget)
+    outs, surfs, reqs = [], [], []
+    for rec, plan, raw in mix:
+        out = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+        surf = torch.zeros(plan.surface_shape(), dtype=torch.float32, device="cuda")
+        outs.append(out)
+        surfs.append(surf)
+        reqs.append((plan, raw, rec.n_samples, out, surf))
+    graph = g.BatchGraph(reqs, scratch_budget=budget)
+    s = torch.cuda.Stream()
+    try:
+        for _ in range(2):
+            for o, sf in zip(outs, surfs):
+                o.zero_()
+                sf.zero_()
+            torch.cuda.synchronize()
+            graph.launch(stream=s)
+            s.synchronize()
+            for o, sf, ro, rs in zip(outs, surfs, ref_outs, ref_surfs):
+                np.testing.assert_array_equal(o.cpu().numpy(), ro.cpu().numpy())
+                np.testing.assert_array_equal(sf.cpu().numpy(), rs.cpu().numpy())
+    finally:
+        graph.close()
+
+
+def test_batch_graph_follows_new_recordings_in_the_same_buffers(g):
+    """Slots refilled with other recordings of the same size: a replay of the
+    unchanged graph acquires the new contents (here, the bytes of each
+    recording shuffled), as gnss_acquire_device does on them."""
+    first = siggen.batch_requests(4, ms_range=(20, 40), seed=7)
+    rng = np.random.default_rng(11)
+    items = []
+    for r1 in first:
+        plan = g.Plan.for_recording(r1)
+        raw = torch.from_numpy(np.ascontiguousarray(r1.raw)).cuda()
+        out = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+        items.append((plan, raw, r1.n_samples, out, None))
+    graph = g.BatchGraph(items)
+    try:
+        graph.launch()
+        torch.cuda.synchronize()
+        for (plan, raw, n, out, _), r1 in zip(items, first):
+            new = np.ascontiguousarray(r1.raw).copy()
+            rng.shuffle(new)  # a different recording of the same size and format
+            raw.copy_(torch.from_numpy(new))
+        graph.launch()
+        torch.cuda.synchronize()
+        for plan, raw, n, out, _ in items:
+            ref = torch.zeros_like(out)
+            plan.acquire_device(raw, n, ref)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+    finally:
+        graph.close()
