@@ -94,8 +94,11 @@ struct XCfg {
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
   static constexpr size_t stage_off = (DB || CL ? 2 : 1) * buf_bytes;
   static constexpr size_t smem = stage_off + (ST ? sizeof(float2) * N : 0);
-  // two CTAs per SM: up to 128 registers at 256 threads, 64 at 512 (E = 8)
-  static constexpr int MINB = (T <= 256 || (E <= 8 && T <= 512)) ? 2 : 1;
+  // CTAs per SM the registers must allow: a budget of 128 registers per
+  // thread (two 256-thread CTAs, four of 128, ...; registers are allocated
+  // per warp, so CTAs under 32 threads count as one warp), 64 at 512 threads
+  // with E = 8
+  static constexpr int MINB = T <= 256 ? 512 / (T < 32 ? 32 : T) : (E <= 8 && T <= 512) ? 2 : 1;
   static_assert(stage_off % 16 == 0, "bulk copies need a 16-byte aligned destination");
 };
 
