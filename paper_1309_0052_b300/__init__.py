@@ -252,10 +252,15 @@ class Plan:
     def surface_shape(self):
         return (self.n_sets, self.n_prn, self.n_dopp, self.N)
 
-    def acquire(self, samples, n_samples: int, surface=None, stream=None) -> np.ndarray:
-        """gnss_acquire.  samples: numpy (host) or CUDA tensor (device).
-        Returns the detection records; synchronises the stream."""
-        out = np.zeros(self.n_prn, DETECTION_DTYPE)
+    def acquire(self, samples, n_samples: int, surface=None, stream=None, out=None) -> np.ndarray:
+        """gnss_acquire.  samples: numpy (host) or CUDA tensor (device).  out:
+        optional host array of n_prn DETECTION_DTYPE records to fill (page-locked
+        memory lets the records come back by an asynchronous copy).  Returns the
+        detection records; synchronises the stream."""
+        if out is None:
+            out = np.zeros(self.n_prn, DETECTION_DTYPE)
+        elif out.dtype != DETECTION_DTYPE or out.shape != (self.n_prn,) or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous array of n_prn DETECTION_DTYPE records")
         on_dev = int(hasattr(samples, "is_cuda") and samples.is_cuda)
         if not on_dev:
             samples = np.ascontiguousarray(samples)

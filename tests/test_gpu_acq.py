@@ -135,6 +135,15 @@ def test_host_device_and_async_paths_agree(g):
     det_async = g.detections_from_bytes(out.cpu().numpy())
     np.testing.assert_array_equal(det_host, det_dev)
     np.testing.assert_array_equal(det_async, det_dev)
+    # caller-owned page-locked record buffer, filled by an asynchronous copy
+    pin = torch.zeros(plan.n_prn * g.DETECTION_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    recs = pin.numpy().view(g.DETECTION_DTYPE)
+    got = plan.acquire(torch.from_numpy(np.ascontiguousarray(rec.raw)).pin_memory().numpy(), rec.n_samples,
+                       stream=s, out=recs)
+    assert got is recs
+    np.testing.assert_array_equal(recs, det_dev)
+    with pytest.raises(ValueError):
+        plan.acquire(np.ascontiguousarray(rec.raw), rec.n_samples, out=np.zeros(plan.n_prn + 1, g.DETECTION_DTYPE))
 
 
 def test_traced_acquisition_same_records_and_ordered_events(g):
