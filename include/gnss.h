@@ -539,11 +539,12 @@ GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
  * 16 needs N <= 16384), and with 16 it can stage the
  * next block's spectrum into shared memory by a bulk TMA copy while the
  * current block is transformed (variant code 16 | GNSS_TUNE_STAGED, offered
- * where the CTA's shared memory still fits: N <= 8192).  At N = 4096 the
- * 16-per-thread form can also run the class-local pass schedule (variant
- * code 16 | GNSS_TUNE_CLASS_LOCAL): after the first radix-16 pass the
- * transform splits into 16 independent 256-point transforms, each on half a
- * warp, so one CTA barrier per block instead of two.  With
+ * where the CTA's shared memory still fits: N <= 8192).  At N = 4096 and
+ * 8192 the 16-per-thread form can also run the class-local pass schedule
+ * (variant code 16 | GNSS_TUNE_CLASS_LOCAL, the default there): after the
+ * first radix-16 pass the transform splits into 16 independent N/16-point
+ * transforms, each on half a warp (4096) or a warp (8192), so one CTA
+ * barrier per block instead of two or three.  With
  * force_elems = 0 every valid variant is timed on a probe shaped like the
  * plan (its Doppler bins up to 32, its sets, 8 blocks) and the fastest is
  * recorded for the plan's FFT size on the current device; with force_elems

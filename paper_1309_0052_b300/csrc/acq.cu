@@ -82,15 +82,15 @@ struct Cfg {
 // Launch configuration of the correlate kernel with E elements per thread
 // (a tuning choice: 16 or 32, see xcorr_variant).  With ST the next block's
 // spectrum is staged into shared memory by a bulk TMA copy (N * 8 bytes more).
-// With CL the transform runs the class-local schedule (N = 4096, E = 16, one
-// CTA barrier per block; fft4096_class_local).
+// With CL the transform runs the class-local schedule (N = 4096 or 8192,
+// E = 16: one CTA barrier per block; fft_class_local).
 template <int N, int E, bool ST = false, bool CL = false>
 struct XCfg {
-  static_assert(!CL || (N == 4096 && E == 16 && !ST), "class-local schedule: N = 4096, 16 per thread");
+  static_assert(!CL || ((N == 4096 || N == 8192) && E == 16 && !ST), "class-local schedule: N = 4096 or 8192");
   static constexpr int T = N / E;
   static constexpr bool TWC = (E <= 16);                        // twiddle bases cached in registers
   static constexpr size_t buf_bytes =
-      sizeof(float2) * (CL ? ClassLocal4096::smem_elems : FftShape<N>::smem_elems);
+      sizeof(float2) * (CL ? ClassLocal<(CL ? N : 4096)>::smem_elems : FftShape<N>::smem_elems);
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
   static constexpr size_t stage_off = (DB || CL ? 2 : 1) * buf_bytes;
   static constexpr size_t smem = stage_off + (ST ? sizeof(float2) * N : 0);
@@ -624,7 +624,7 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh
     if constexpr (CL) {
       // one buffer per block, alternating: the next block's first-pass stores
       // go to the other buffer, so no barrier guards this block's last reads
-      fft4096_class_local<true>(v, j, phase ? buf1 : buf0, tw);
+      fft_class_local<N, true>(v, j, phase ? buf1 : buf0, tw);
       phase ^= 1;
     } else if constexpr (TWC) {
       fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw);
@@ -707,7 +707,7 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   __shared__ int s_stage_fail;
   const int j = threadIdx.x;
   // thread j ends each transform holding |R|^2 of phases jo + T r
-  const int jo = CL ? ClassLocal4096::perm(j) : j;
+  const int jo = CL ? ClassLocal<(CL ? N : 4096)>::perm(j) : j;
   const int p = tile % a.P, d = tile / a.P;
   const float2* cp = a.cspec + (size_t)p * N;
   // bin d's spectrum: its own row, or its class's row read K bins further
@@ -900,7 +900,7 @@ cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const i
 static int g_xcorr_e[128][15];
 
 int xcorr_default_e(int N) {
-  if (N == 4096) return 16 | (int)GNSS_TUNE_CLASS_LOCAL;
+  if (N == 4096 || N == 8192) return 16 | (int)GNSS_TUNE_CLASS_LOCAL;
   return N >= 16384 ? 32 : 16;
 }
 
@@ -919,7 +919,7 @@ static bool stage_fits(int N) {
 
 bool xcorr_valid_e(int N, int code) {
   if (code == (16 | (int)GNSS_TUNE_STAGED)) return N / 16 <= 1024 && stage_fits(N);
-  if (code == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return N == 4096;
+  if (code == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return N == 4096 || N == 8192;
   return (code == 16 && N / 16 <= 1024) || (code == 32 && N >= 1024) || (code == 8 && N / 8 <= 1024);
 }
 
@@ -967,7 +967,7 @@ static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t s
   if constexpr (StageFits<N>::value) {
     if (v == (16 | (int)GNSS_TUNE_STAGED)) return xcorr_ne<N, 16, true>(s, a, stream);
   }
-  if constexpr (N == 4096) {
+  if constexpr (N == 4096 || N == 8192) {
     if (v == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return xcorr_ne<N, 16, false, true>(s, a, stream);
   }
   return xcorr_ne<N, 16, false>(s, a, stream);
@@ -1070,7 +1070,7 @@ static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
   if constexpr (StageFits<N>::value) {
     if (v == (16 | (int)GNSS_TUNE_STAGED)) return xcorr_batch_ne<N, 16, true>(g, stream);
   }
-  if constexpr (N == 4096) {
+  if constexpr (N == 4096 || N == 8192) {
     if (v == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return xcorr_batch_ne<N, 16, false, true>(g, stream);
   }
   return xcorr_batch_ne<N, 16, false>(g, stream);

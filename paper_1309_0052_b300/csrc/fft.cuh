@@ -504,41 +504,72 @@ __device__ __forceinline__ void fft_block_tw(float2 (&v)[E], int j, float2* buf0
 namespace gnss {
 
 // ---------------------------------------------------------------------------
-// Class-local schedule of the 4096-point transform (16 elements per thread,
-// 256 threads): one CTA-wide exchange per transform instead of two.
+// Class-local schedule (16 elements per thread, T = N / 16 threads, N = 4096
+// or 8192): one CTA-wide exchange per transform instead of P - 1.
 //
-// The first radix-16 pass (inputs at stride 256, straight from registers)
+// The first radix-16 pass (inputs at stride T, straight from registers)
 // writes its output digit c into slot i with i mod 16 = c.  Every later
-// Stockham pass reads x[J + 256 s] and writes y[(J / NS) 16 NS + k + t NS]
-// with NS a multiple of 16, so it maps slots of one residue class c = J mod
-// 16 onto the same class: the rest of the transform is 16 independent
-// 256-point transforms, one per class.  Butterfly J of those passes runs on
-// thread t = 16 (J mod 16) + J / 16, so class c lives on the 16 lanes
-// 16c .. 16c + 15 (half a warp); after the CTA barrier of the first exchange
-// the second exchange needs only __syncwarp, in place in the same buffer
-// (each half-warp reads its class's slots, then overwrites exactly them).
-// On exit thread t holds X[jp + 256 r] in v[r], jp = (t >> 4) + 16 (t & 15).
+// Stockham pass reads x[J + T s'] and writes y[(J / NS) NS R + k + t NS] with
+// NS a multiple of 16, so it maps slots of one residue class c = J mod 16 onto
+// the same class: the rest of the transform is 16 independent T-point
+// transforms, one per class.  In those passes thread t runs the butterflies
+// J = jp + T q, jp = t / G + 16 (t mod G), G = T / 16, so class c = jp mod 16
+// = t / G lives on the G lanes G c .. G c + G - 1 (half a warp at 4096, a
+// warp at 8192); after
+// the CTA barrier of the first exchange the later exchanges need only
+// __syncwarp, in place in the same buffer (each class's lanes read its
+// slots, then overwrite exactly them).  On exit thread t holds X[jp + T r]
+// in v[r].
 //
-// Shared-memory slot of element i: i + i/16 + i/256.  Lanes of a half-warp
-// then hit distinct bank pairs in all four access patterns (first-pass
-// stores at 16 t + u, class gathers at jp + 256 r, second-pass stores at
-// 256 (jp / 16) + jp mod 16 + 16 u), and every access is a per-thread base
-// plus a compile-time offset.
+// Shared-memory slot of element i: i + i/16 + i/256.  The lanes of each
+// half-warp then hit distinct bank pairs in every access of the schedule
+// (first-pass stores at 16 t + u, class gathers at jp + T r, later stores at
+// (J / NS) 16 NS + k + u NS), and every access is a per-thread base plus a
+// compile-time offset.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int pad_cl(int i) { return i + (i >> 4) + (i >> 8); }
+// pad_cl(x + d) - pad_cl(x) for the strides d of the schedule (no carries)
+__host__ __device__ constexpr int cl_off(int d) { return d + d / 16 + d / 256; }
 
-struct ClassLocal4096 {
-  static constexpr int N = 4096, E = 16, T = 256;
+template <int N>
+struct ClassLocal {
+  static_assert(N == 4096 || N == 8192, "class-local schedule: N = 4096 or 8192, 16 per thread");
+  static constexpr int E = 16, T = N / E, G = T / 16;
   static constexpr int smem_elems = N + N / 16 + N / 256;  // > pad_cl(N - 1)
-  // thread of butterfly J in the class passes (an involution on [0, 256))
-  __device__ __forceinline__ static int perm(int t) { return (t >> 4) + 16 * (t & 15); }
+  // thread of butterfly J (mod T) in the class passes (an involution when G = 16)
+  __device__ __forceinline__ static int perm(int t) { return t / G + 16 * (t % G); }
 };
 
-template <bool INV, typename Hook = NoHook>
-__device__ __forceinline__ void fft4096_class_local(float2 (&v)[16], int t, float2* __restrict__ buf,
-                                                    const FftTw<4096, 16, INV>& tw, const Hook& hook = Hook()) {
-  // pass 1 (NS = 1): DFT16 over stride 256; outputs to 16 t + u
-  pass_compute_tw<4096, 16, 16, 1, INV>(v, tw);
+template <int N, bool INV, int NS>
+__device__ __forceinline__ void class_local_rest(float2 (&v)[16], int jp, float2* buf, const float2* g,
+                                                 const FftTw<N, 16, INV, NS>& tw) {
+  // g = buf + pad_cl(jp): both address the same exchange buffer (no restrict)
+  constexpr int T = N / 16;
+  constexpr int R = PassRadix<N, NS, 16>::value;
+  constexpr int Q = 16 / R;
+  pass_compute_tw<N, 16, R, NS, INV>(v, tw);
+  if constexpr (NS * R < N) {
+    __syncwarp();  // the class's lanes have read every slot of the class
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const unsigned J = (unsigned)(jp + T * q);
+      float2* b = buf + pad_cl((int)((J / NS) * NS * R + (J & (NS - 1))));
+#pragma unroll
+      for (int t = 0; t < R; ++t) b[cl_off(t * NS)] = v[q + Q * t];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = g[cl_off(T * r)];
+    class_local_rest<N, INV, NS * R>(v, jp, buf, g, tw.next);
+  }
+}
+
+template <int N, bool INV, typename Hook = NoHook>
+__device__ __forceinline__ void fft_class_local(float2 (&v)[16], int t, float2* buf, const FftTw<N, 16, INV>& tw,
+                                                const Hook& hook = Hook()) {
+  constexpr int T = N / 16;
+  // pass 1 (NS = 1): DFT16 over stride T; outputs to 16 t + u
+  pass_compute_tw<N, 16, 16, 1, INV>(v, tw);
   {
     float2* b = buf + pad_cl(16 * t);
 #pragma unroll
@@ -546,24 +577,11 @@ __device__ __forceinline__ void fft4096_class_local(float2 (&v)[16], int t, floa
   }
   __syncthreads();
   hook();
-  const int jp = ClassLocal4096::perm(t);
-  const float2* g = buf + pad_cl(jp);  // element jp + 256 r sits at g[273 r]
+  const int jp = ClassLocal<N>::perm(t);
+  const float2* g = buf + pad_cl(jp);  // element jp + T r sits at g[cl_off(T r)]
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = g[273 * r];
-  // pass 2 (NS = 16), butterfly jp: twiddles of k = jp mod 16
-  pass_compute_tw<4096, 16, 16, 16, INV>(v, tw.next);
-  __syncwarp();  // the half-warp has read every slot of its class
-  {
-    // output u of butterfly jp goes to 256 (jp / 16) + jp mod 16 + 16 u
-    float2* b = buf + pad_cl(256 * (jp >> 4) + (jp & 15));
-#pragma unroll
-    for (int u = 0; u < 16; ++u) b[17 * u] = v[u];
-  }
-  __syncwarp();
-#pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = g[273 * r];
-  // pass 3 (NS = 256), butterfly jp: twiddles of k = jp
-  pass_compute_tw<4096, 16, 16, 256, INV>(v, tw.next.next);
+  for (int r = 0; r < 16; ++r) v[r] = g[cl_off(T * r)];
+  class_local_rest<N, INV, 16>(v, jp, buf, g, tw.next);
 }
 
 }  // namespace gnss

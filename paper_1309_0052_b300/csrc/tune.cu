@@ -30,7 +30,7 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
   if (force_elems) {
     if (!xcorr_valid_e(N, (int)force_elems))
       return fail_status(GNSS_EINVAL, "variant must be 8 (N <= 8192), 16 (N <= 16384), 32 (N >= 1024), 16 | GNSS_TUNE_STAGED "
-                                      "(N <= 8192) or 16 | GNSS_TUNE_CLASS_LOCAL (N = 4096)");
+                                      "(N <= 8192) or 16 | GNSS_TUNE_CLASS_LOCAL (N = 4096 or 8192)");
     set_xcorr_variant(N, (int)force_elems);
     res.chosen = force_elems;
     if (out) *out = res;

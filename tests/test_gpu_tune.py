@@ -43,7 +43,7 @@ def _valid(N):
         v.append(16 | STAGED)
     if N <= 8192:
         v.append(8)
-    if N == 4096:
+    if N in (4096, 8192):
         v.append(16 | CLASS_LOCAL)
     return v
 
@@ -59,7 +59,7 @@ def test_every_shape_matches_oracle(g, N, half, B):
     x = oracle.unpack(raw, n, fmt)
     S = oracle.surfaces(x, N * 1000, coh, B, half, prns, dopp[0] + dopp[1] * np.arange(dopp[2]), 8)
     ref = oracle.detect(S, prns)
-    default = 32 if N >= 16384 else (16 | CLASS_LOCAL) if N == 4096 else 16
+    default = 32 if N >= 16384 else (16 | CLASS_LOCAL) if N in (4096, 8192) else 16
     try:
         for elems in _valid(N):
             assert plan.autotune(elems)["chosen"] == elems
@@ -85,7 +85,7 @@ def test_invalid_shape_rejected(g):
         big.autotune(16 | STAGED)  # the stage does not fit beside the 16384-point exchange buffer
     assert e.value.status == g.EINVAL
     with pytest.raises(g.GnssError) as e:
-        big.autotune(16 | CLASS_LOCAL)  # the class-local schedule is built for N = 4096 only
+        big.autotune(16 | CLASS_LOCAL)  # the class-local schedule is built for N = 4096 and 8192
     assert e.value.status == g.EINVAL
 
 
