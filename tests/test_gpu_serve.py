@@ -58,7 +58,14 @@ def test_results_in_the_mix_equal_results_alone(g, recs, alone):
         np.testing.assert_array_equal(srv.wait(t, 60000), alone[k])
     st = srv.stats()
     assert st["completed"] == len(recs) and st["failed"] == 0 and st["queued"] == 0
-    assert st["batches"] < len(recs)  # requests shared launches
+    # a burst: the requests submitted while the first one is on the GPU are
+    # admitted together (continuous batching), whatever the kernels' speed
+    burst = [srv.submit(g.Server.desc_for(r), r.raw, r.n_samples) for r in recs]
+    for k, t in enumerate(burst):
+        np.testing.assert_array_equal(srv.wait(t, 60000), alone[k])
+    st2 = srv.stats()
+    assert st2["completed"] == 2 * len(recs) and st2["failed"] == 0
+    assert st2["batches"] - st["batches"] < len(recs)  # requests shared launches
     srv.close()
 
 
