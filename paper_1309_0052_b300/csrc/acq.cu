@@ -80,7 +80,7 @@ struct Cfg {
 };
 
 // Launch configuration of the correlate kernel with E elements per thread
-// (a tuning choice: 16 or 32, see xcorr_variant).  With ST the next block's
+// (a tuning choice: 8, 16 or 32, see xcorr_variant).  With ST the next block's
 // spectrum is staged into shared memory by a bulk TMA copy (N * 8 bytes more).
 // With CL the transform runs the class-local schedule (N = 4096 or 8192,
 // E = 16: one CTA barrier per block; fft_class_local).
