@@ -34,20 +34,31 @@ struct EvalOut {
   float P, gf, gt;
 };
 
-template <int T>
-__device__ __forceinline__ float block_sum(float v, float* red) {
+// Sums of K per-thread values over the CTA, all in one pass: a warp shuffle
+// tree per value, one shared-memory exchange (red holds 32 K floats) and the
+// warps' partial sums added in warp order -- per value the same order as K
+// separate reductions, with two CTA barriers instead of 2 K.
+template <int T, int K>
+__device__ __forceinline__ void block_sums(float (&v)[K], float* red) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   constexpr int W = T / 32;
   if constexpr (W > 1) {
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    v = 0.f;
+    if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int w = 0; w < W; ++w) v += red[w];
+      for (int k = 0; k < K; ++k) red[k * 32 + (threadIdx.x >> 5)] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      v[k] = 0.f;
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[k] += red[k * 32 + w];
+    }
   }
-  return v;
 }
 
 // Samples [n0, n0 + 8) as floats.
@@ -165,15 +176,24 @@ __device__ EvalOut evaluate(const RefineJob& J, const CodeBits& cb, double f, do
     }
   }
   EvalOut o;
-  zr = block_sum<T>(zr * cb.scale, red);
-  zi = block_sum<T>(zi * cb.scale, red);
+  if constexpr (GRAD) {
+    float sums[6] = {zr * cb.scale, zi * cb.scale, fr * cb.scale, fi * cb.scale, tr * cb.scale, tii * cb.scale};
+    block_sums<T, 6>(sums, red);
+    zr = sums[0];
+    zi = sums[1];
+    fr = sums[2];
+    fi = sums[3];
+    tr = sums[4];
+    tii = sums[5];
+  } else {
+    float sums[2] = {zr * cb.scale, zi * cb.scale};
+    block_sums<T, 2>(sums, red);
+    zr = sums[0];
+    zi = sums[1];
+  }
   o.P = zr * zr + zi * zi;
   o.gf = o.gt = 0.f;
   if constexpr (GRAD) {
-    fr = block_sum<T>(fr * cb.scale, red);
-    fi = block_sum<T>(fi * cb.scale, red);
-    tr = block_sum<T>(tr * cb.scale, red);
-    tii = block_sum<T>(tii * cb.scale, red);
     // dz/df -> (-j 2 pi / fs) sum (n - L/2) w ctilde = (2 pi / fs) (fi - j fr)
     const float g = (float)(2.0 * 3.14159265358979323846 / J.fs);
     const float dfr = g * fi, dfi = -g * fr;
@@ -203,7 +223,7 @@ __global__ void __launch_bounds__(T) k_refine_eval(RefineJob J, const int* __res
                                                   const double* __restrict__ tau, float* __restrict__ P,
                                                   float* __restrict__ dPdf, float* __restrict__ dPdtau) {
   __shared__ CodeBits chips;
-  __shared__ float red[32];
+  __shared__ float red[32 * 6];
   load_chips<T>(J, prn[blockIdx.x], chips);
   const EvalOut o = evaluate<T, FMT, true>(J, chips, f[blockIdx.x], tau[blockIdx.x], red);
   if (threadIdx.x == 0) {
@@ -237,7 +257,7 @@ template <int T, int FMT>
 __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate* __restrict__ cands, int max_iter,
                                              double search_hz, gnss_refined* __restrict__ out) {
   __shared__ CodeBits chips;
-  __shared__ float red[32];
+  __shared__ float red[32 * 6];
   const gnss_candidate c = cands[blockIdx.x];
   load_chips<T>(J, c.prn, chips);
   const double c1 = 1e-4, tol_tau = 1e-5, tol_f = 1e-3;
