@@ -486,13 +486,28 @@ __device__ __forceinline__ uint32_t block_min_u32(uint32_t v, uint32_t* s_idx) {
 // peak = max S, tau = the smallest phase holding it, second = max S over the
 // phases whose circular distance to tau exceeds excl (0 if none).  Only the
 // threads whose own maximum is the peak search their phases for it, and only
-// the threads holding a phase inside the band (with 2 excl + 1 <= T at most
-// one per thread, the phases of a thread being T apart) scan their cells for
-// the second peak; every other thread's contribution is its own maximum.
-template <int N, int E>
+// the threads that can hold a phase inside the band (their phases are
+// congruent modulo a period P >= 2 excl + 1, so the band meets a thread only
+// if its residue lies within excl of tau's) scan their cells for the second
+// peak; every other thread's contribution is its own maximum.
+// Phase held in accumulator r by the thread with butterfly index j: j + T r,
+// or the class-local schedule's output order.  Phases grow with r, and all
+// phases of a thread are congruent to j modulo 'period'.
+template <int N, int E, bool CL>
+struct PhaseMap {
+  static constexpr bool pairs = CL && N == 8192;
+  static constexpr int period = pairs ? 256 : N / E;
+  __device__ __forceinline__ static int at(int j, int r) {
+    if constexpr (pairs) return ClassLocal<8192>::out_index(j, r);
+    else return j + (N / E) * r;
+  }
+};
+
+template <int N, int E, bool CL>
 __device__ __forceinline__ void row_stats(const float (&a)[E], int j, int excl, float* s_val, uint32_t* s_idx,
                                           RowStat* out) {
   constexpr int T = N / E;
+  using M = PhaseMap<N, E, CL>;
   float tmax = a[0];
 #pragma unroll
   for (int r = 1; r < E; ++r) tmax = fmaxf(tmax, a[r]);
@@ -501,15 +516,15 @@ __device__ __forceinline__ void row_stats(const float (&a)[E], int j, int excl, 
   if (tmax == best) {
 #pragma unroll
     for (int r = E - 1; r >= 0; --r)
-      if (a[r] == best) bt = (uint32_t)(j + T * r);
+      if (a[r] == best) bt = (uint32_t)M::at(j, r);
   }
   bt = block_min_u32<T>(bt, s_idx);
   float sec = tmax;
-  if (2 * excl + 1 > T || ((j - (int)bt + excl) & (T - 1)) <= 2 * excl) {
+  if (2 * excl + 1 > M::period || ((j - (int)bt + excl) & (M::period - 1)) <= 2 * excl) {
     sec = 0.f;  // every cell is >= 0
 #pragma unroll
     for (int r = 0; r < E; ++r) {
-      int dist = abs(j + T * r - (int)bt);
+      int dist = abs(M::at(j, r) - (int)bt);
       dist = min(dist, N - dist);
       if (dist > excl) sec = fmaxf(sec, a[r]);
     }
@@ -706,7 +721,7 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ int s_stage_fail;
   const int j = threadIdx.x;
-  // thread j ends each transform holding |R|^2 of phases jo + T r
+  // thread j ends each transform holding |R|^2 of phases PhaseMap::at(jo, r)
   const int jo = CL ? ClassLocal<(CL ? N : 4096)>::perm(j) : j;
   const int p = tile % a.P, d = tile / a.P;
   const float2* cp = a.cspec + (size_t)p * N;
@@ -719,7 +734,9 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   uint32_t parity = 0;
   bool stage_ok = true;
   FftTw<N, E, true> tw;
-  if constexpr (TWC) tw.init(jo);  // the first pass has no twiddles; later passes run butterfly jo
+  // the first pass has no twiddles; later passes run butterfly jo
+  if constexpr (CL) ClassLocal<(CL ? N : 4096)>::init_twiddles(tw, jo);
+  else if constexpr (TWC) tw.init(jo);
   griddep_wait();  // the spectra and the cleared counters are complete and visible
   if constexpr (ST) {
     if (j == 0) {
@@ -752,9 +769,9 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
     if (a.surface != nullptr) {
       float* row = a.surface + (((size_t)set * a.P + p) * a.D + d) * (size_t)N;
 #pragma unroll
-      for (int r = 0; r < E; ++r) row[jo + T * r] = acc[r];
+      for (int r = 0; r < E; ++r) row[PhaseMap<N, E, CL>::at(jo, r)] = acc[r];
     }
-    row_stats<N, E>(acc, jo, a.excl, s_val, s_idx, a.rows + ((size_t)set * a.P + p) * a.D + d);
+    row_stats<N, E, CL>(acc, jo, a.excl, s_val, s_idx, a.rows + ((size_t)set * a.P + p) * a.D + d);
   }
   if constexpr (ST) {
     // A wait that gave up may leave a copy in flight: wait for it once more

@@ -519,7 +519,19 @@ namespace gnss {
 // the CTA barrier of the first exchange the later exchanges need only
 // __syncwarp, in place in the same buffer (each class's lanes read its
 // slots, then overwrite exactly them).  On exit thread t holds X[jp + T r]
-// in v[r].
+// in v[r] at N = 4096.
+//
+// At N = 8192 the last pass is radix 2 (NS = 4096), and its two inputs
+// y[m], y[m + 4096] come out of the radix-16 pass before it in the same
+// register of lanes l and l ^ 16 (butterflies J and J + 256 of one class).
+// The lane pair splits the 16 butterflies m = k + 256 t, k = jp mod 256: the
+// low lane takes t < 8, the high lane t >= 8, and each sends the other the 8
+// operands it needs by shuffle -- half the data moves, and no shared-memory
+// exchange is left for that pass.  Thread t then holds X[b + 256 (r mod 8) +
+// 4096 (r / 8)] in v[r], b = k + 2048 h, h = 1 on the high lane
+// (ClassLocal::out_index).  Each butterfly keeps its twiddle (the same float
+// argument of sincospif) and its arithmetic, so the results are those of the
+// exchanged form bit for bit.
 //
 // Shared-memory slot of element i: i + i/16 + i/256.  The lanes of each
 // half-warp then hit distinct bank pairs in every access of the schedule
@@ -538,7 +550,48 @@ struct ClassLocal {
   static constexpr int smem_elems = N + N / 16 + N / 256;  // > pad_cl(N - 1)
   // thread of butterfly J (mod T) in the class passes (an involution when G = 16)
   __device__ __forceinline__ static int perm(int t) { return t / G + 16 * (t % G); }
+  // first output of the lane-pair radix-2 butterflies of class index jp (N = 8192)
+  __device__ __forceinline__ static int pair_base(int jp) { return (jp & 255) + 2048 * ((jp >> 8) & 1); }
+  // element of X that class index jp holds in v[r] on exit: increasing in r,
+  // and congruent to jp modulo 256 at both sizes
+  __device__ __forceinline__ static int out_index(int jp, int r) {
+    if constexpr (N == 8192) return pair_base(jp) + 256 * (r & 7) + 4096 * (r >> 3);
+    else return jp + T * r;
+  }
+  // twiddle bases of every pass for class index jp; at 8192 the lane-pair
+  // radix-2 pass runs butterflies pair_base(jp) + 256 i, i < 8
+  template <bool INV>
+  __device__ __forceinline__ static void init_twiddles(FftTw<N, 16, INV>& tw, int jp) {
+    tw.init(jp);
+    if constexpr (N == 8192) {
+      auto& last = tw.next.next.next;  // NS = 4096, radix 2
+      constexpr float scale = (INV ? 2.f : -2.f) / float(N);
+      const int b = pair_base(jp);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) last.tw[i].init(scale * float(b + 256 * i));
+    }
+  }
 };
+
+// The radix-2 pass of N = 8192 across lanes l and l ^ 16 (see above).
+template <bool INV>
+__device__ __forceinline__ void lane_pair_radix2(float2 (&v)[16], int jp, const FftTw<8192, 16, INV, 4096>& tw) {
+  const bool hi = (jp >> 8) & 1;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 send = hi ? v[i] : v[8 + i];
+    float2 got;
+    got.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+    got.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+    float2 u[2];
+    u[0] = hi ? got : v[i];
+    u[1] = hi ? v[8 + i] : got;
+    TwApply<2, 1, true>::run(u, tw.tw[i]);
+    dft_r<2, INV>(u);
+    v[i] = u[0];
+    v[8 + i] = u[1];
+  }
+}
 
 template <int N, bool INV, int NS>
 __device__ __forceinline__ void class_local_rest(float2 (&v)[16], int jp, float2* buf, const float2* g,
@@ -548,7 +601,9 @@ __device__ __forceinline__ void class_local_rest(float2 (&v)[16], int jp, float2
   constexpr int R = PassRadix<N, NS, 16>::value;
   constexpr int Q = 16 / R;
   pass_compute_tw<N, 16, R, NS, INV>(v, tw);
-  if constexpr (NS * R < N) {
+  if constexpr (N == 8192 && NS * R == N / 2) {
+    lane_pair_radix2<INV>(v, jp, tw.next);
+  } else if constexpr (NS * R < N) {
     __syncwarp();  // the class's lanes have read every slot of the class
 #pragma unroll
     for (int q = 0; q < Q; ++q) {

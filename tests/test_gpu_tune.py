@@ -134,20 +134,31 @@ def test_staged_full_size_and_batch(g):
         plan.autotune(16 | CLASS_LOCAL)
 
 
-def test_class_local_matches_two_barrier_schedule(g):
-    """The class-local schedule (the default at N = 4096) runs the same
-    butterflies with the same operands as the two-barrier schedule, only on
-    other threads, so on the full 100 ms workload both give identical
-    surfaces and records."""
+def _weak_100ms(g):
     rec = siggen.weak_100ms()
-    plan = g.Plan.for_recording(rec)
-    raw = torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda()
+    return g.Plan.for_recording(rec), rec.raw, rec.n_samples
+
+
+def _fs_8192(g):
+    raw, n = _recording(8192, 2, 10, siggen.FMT_2BIT_IQ, 8192)
+    return g.Plan(8_192_000, 2, -10000, 500, 41, prns=range(1, 33), half_bit=False, fmt=siggen.FMT_2BIT_IQ), raw, n
+
+
+@pytest.mark.parametrize("make", [_weak_100ms, _fs_8192])
+def test_class_local_matches_two_barrier_schedule(g, make):
+    """The class-local schedule (the default at N = 4096 and 8192) runs the
+    same butterflies with the same operands as the two-barrier schedule, only
+    on other threads -- at 8192 the last radix-2 pass across lane pairs by
+    shuffle -- so both give identical surfaces and records: the full 100 ms
+    workload at 4096, 20 ms at 8.192 MHz with 32 PRNs and 41 bins."""
+    plan, raw_np, n = make(g)
+    raw = torch.from_numpy(np.ascontiguousarray(raw_np)).cuda()
     res = {}
     try:
         for code in (16, 16 | CLASS_LOCAL):
             plan.autotune(code)
             surf = torch.zeros(plan.surface_shape(), dtype=torch.float32, device="cuda")
-            det = plan.acquire(raw, rec.n_samples, surface=surf)
+            det = plan.acquire(raw, n, surface=surf)
             res[code] = (det, surf.cpu().numpy())
     finally:
         plan.autotune(16 | CLASS_LOCAL)
