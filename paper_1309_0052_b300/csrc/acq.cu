@@ -14,6 +14,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cooperative_groups.h>
 #include <mutex>
 
 #include "fft.cuh"
@@ -300,12 +301,15 @@ __device__ __forceinline__ void fold_tile(const FoldArgs& a, int tile) {
 
 // Request of a batched launch that owns CTA blockIdx.x: base[r] <= blockIdx.x
 // < base[r + 1] (base ascending, base[0] = 0).  One probe per thread.
-__device__ __forceinline__ int find_request(const uint32_t* __restrict__ base, int n) {
+__device__ __forceinline__ int find_request(const uint32_t* __restrict__ base, int n, unsigned tile) {
   __shared__ int s_req;
   for (int r = threadIdx.x; r < n; r += blockDim.x)
-    if (__ldg(base + r) <= blockIdx.x && blockIdx.x < __ldg(base + r + 1)) s_req = r;
+    if (__ldg(base + r) <= tile && tile < __ldg(base + r + 1)) s_req = r;
   __syncthreads();
   return s_req;
+}
+__device__ __forceinline__ int find_request(const uint32_t* __restrict__ base, int n) {
+  return find_request(base, n, blockIdx.x);
 }
 
 template <int N, int FMT>
@@ -829,6 +833,214 @@ __global__ void __launch_bounds__(XCfg<N, E, ST, CL>::T, XCfg<N, E, ST, CL>::MIN
 }
 
 // ---------------------------------------------------------------------------
+// N = 16384 over a cluster of two CTAs (the split correlate variant).  The
+// inverse FFT of Section 3 is split once by decimation in time: with
+// x = Y conj(C) and M = N / 2,
+//   X[2q + h] = sum_{k < M} z_h[k] e^{2 pi i k q / M},
+//   z_0[k] = x[k] + x[k + M],   z_1[k] = (x[k] - x[k + M]) e^{2 pi i k / N},
+// so CTA h of the pair (its rank in the cluster) sums |X[2q + h]|^2 with the
+// 8192-point class-local transform: 16 accumulators per thread and no spills,
+// where one 16384-point CTA holds 32 elements and 32 sums per thread.  Each
+// CTA reads both halves of Y and C and forms the products it needs (handing
+// the halves over through distributed shared memory instead took two
+// cluster barriers per block and ran 40% slower).  The pair merges its row
+// statistics through distributed shared memory: the row's peak and the
+// smallest phase holding it, then each half's maximum outside the band
+// around that phase.
+// ---------------------------------------------------------------------------
+// cos(pi m / 16), 0 <= m <= 8 (mathematical constants)
+__device__ __forceinline__ float cos_pi16(int m) {
+  return m == 0 ? 1.f
+       : m == 1 ? 0.98078528040323044913f
+       : m == 2 ? 0.92387953251128675613f
+       : m == 3 ? 0.83146961230254523708f
+       : m == 4 ? 0.70710678118654752440f
+       : m == 5 ? 0.55557023301960222474f
+       : m == 6 ? 0.38268343236508977173f
+       : m == 7 ? 0.19509032201612826785f
+                : 0.f;
+}
+// e^{i pi r / 16}, 0 <= r < 16
+__device__ __forceinline__ float2 rot32(int r) {
+  return r <= 8 ? make_float2(cos_pi16(r), cos_pi16(8 - r)) : make_float2(-cos_pi16(16 - r), cos_pi16(r - 8));
+}
+
+struct SplitCfg {
+  static constexpr int N = 16384, M = 8192, T = 512;
+  static constexpr size_t smem = 2 * sizeof(float2) * ClassLocal<M>::smem_elems;  // ping-pong exchange buffers
+};
+
+// One block: thread j forms z_h at k = j + 512 r (the 8192-point input
+// layout; e^{2 pi i k / N} = wj e^{i pi r / 16}, wj = e^{2 pi i j / N}),
+// transforms it and adds |.|^2.  Only the last element of the upper half can
+// wrap around the row (ksh < 16).
+template <int H>
+__device__ __forceinline__ void split_block(const float2* __restrict__ y, int ksh, const float2* __restrict__ cp,
+                                            int j, float2* buf, FftTw<8192, 16, true>& tw, float2 wj,
+                                            float (&acc)[16]) {
+  constexpr int N = SplitCfg::N, M = SplitCfg::M, T = SplitCfg::T;
+  tw.launder();
+  asm volatile("" : "+l"(cp));
+  const float2* ys = y + j + ksh;
+  const float2* cs = cp + j;
+  float2 v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const float2 lo = c_mulconj(__ldcg(ys + T * r), __ldg(cs + T * r));
+    const int kb = j + ksh + T * r + M;
+    const float2 hi = c_mulconj(__ldcg(y + (r < 15 || kb < N ? kb : kb - N)), __ldg(cs + T * r + M));
+    if constexpr (H == 0) v[r] = c_add(lo, hi);
+    else v[r] = c_mul(c_sub(lo, hi), c_mul(wj, rot32(r)));
+  }
+  fft_class_local<M, true>(v, j, buf, tw);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
+}
+
+template <bool HALF>
+__device__ __forceinline__ void xcorr_tile_split(const XcorrArgs& a, int tile, float2* sm) {
+  namespace cg = cooperative_groups;
+  constexpr int N = SplitCfg::N, M = SplitCfg::M, T = SplitCfg::T;
+  constexpr int S = HALF ? 2 : 1;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int h = (int)cluster.block_rank();  // the parity of the phases this CTA sums
+  float2* buf0 = sm;
+  float2* buf1 = sm + ClassLocal<M>::smem_elems;
+  __shared__ float s_val[32];
+  __shared__ uint32_t s_idx[32];
+  __shared__ float s_peak, s_sec;  // read by the other CTA of the pair
+  __shared__ uint32_t s_tau;
+  const int j = threadIdx.x;
+  const int jo = ClassLocal<M>::perm(j);  // thread j ends holding X_h[out_index(jo, r)]
+  const int p = tile % a.P, d = tile / a.P;
+  const float2* cp = a.cspec + (size_t)p * N;
+  const float2* yd = a.Y + (size_t)(a.bin_cls ? __ldg(a.bin_cls + d) : d) * a.B * N;
+  const int ksh = a.bin_shift ? __ldg(a.bin_shift + d) : 0;
+  FftTw<M, 16, true> tw;
+  ClassLocal<M>::init_twiddles(tw, jo);
+  float2 wj;
+  sincospif(2.f * (float)j / (float)N, &wj.y, &wj.x);
+  griddep_wait();  // the spectra and the cleared counters are complete and visible
+  int phase = 0;
+#pragma unroll 1
+  for (int set = 0; set < S; ++set) {
+    float acc[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] = 0.f;
+    for (int b = set; b < a.B; b += S) {
+      // one buffer per transform, alternating (no barrier guards the last reads)
+      float2* buf = phase ? buf1 : buf0;
+      if (h == 0) split_block<0>(yd + (size_t)b * N, ksh, cp, j, buf, tw, wj, acc);
+      else split_block<1>(yd + (size_t)b * N, ksh, cp, j, buf, tw, wj, acc);
+      phase ^= 1;
+    }
+    constexpr float sc = 1.f / ((float)N * (float)N);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] *= sc;
+    if (a.surface != nullptr) {
+      float* row = a.surface + (((size_t)set * a.P + p) * a.D + d) * (size_t)N;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) row[2 * ClassLocal<M>::out_index(jo, r) + h] = acc[r];
+    }
+    // this half's peak and the smallest phase holding it
+    float tmax = acc[0];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) tmax = fmaxf(tmax, acc[r]);
+    float best = block_max<T>(tmax, s_val);
+    uint32_t bt = 0xffffffffu;
+    if (tmax == best) {
+#pragma unroll
+      for (int r = 15; r >= 0; --r)
+        if (acc[r] == best) bt = (uint32_t)(2 * ClassLocal<M>::out_index(jo, r) + h);
+    }
+    bt = block_min_u32<T>(bt, s_idx);
+    if (j == 0) {
+      s_peak = best;
+      s_tau = bt;
+    }
+    cluster.sync();
+    {
+      const float ob = *cluster.map_shared_rank(&s_peak, h ^ 1);
+      const uint32_t ot = *cluster.map_shared_rank(&s_tau, h ^ 1);
+      if (ob > best || (ob == best && ot < bt)) {
+        best = ob;
+        bt = ot;
+      }
+    }
+    // this half's maximum outside the band around the row's peak phase: the
+    // phases of thread j are all 2 jo + h modulo 512 (> 2 excl + 1)
+    float sec = tmax;
+    if (2 * a.excl + 1 > 512 || ((2 * jo + h - (int)bt + a.excl) & 511) <= 2 * a.excl) {
+      sec = 0.f;  // every cell is >= 0
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        int dist = abs(2 * ClassLocal<M>::out_index(jo, r) + h - (int)bt);
+        dist = min(dist, N - dist);
+        if (dist > a.excl) sec = fmaxf(sec, acc[r]);
+      }
+    }
+    sec = block_max<T>(sec, s_val);
+    if (j == 0) s_sec = sec;
+    cluster.sync();
+    sec = fmaxf(sec, *cluster.map_shared_rank(&s_sec, h ^ 1));
+    if (h == 0 && j == 0) {
+      RowStat rs;
+      rs.peak = best;
+      rs.tau = bt;
+      rs.second = sec;
+      rs.pad = 0;
+      a.rows[((size_t)set * a.P + p) * a.D + d] = rs;
+    }
+  }
+  // neither CTA leaves while the other may still read its shared memory
+  cluster.sync();
+  if (h != 0) return;
+  // CTA 0 of the pair counts the row for its PRN; the last one detects (as
+  // in xcorr_tile).  The cluster barrier ordered CTA 1's surface writes
+  // before this CTA's fence.
+  __shared__ unsigned s_last;
+  __syncthreads();
+  if (a.second_whole) {
+    if (j == 0) {
+      __threadfence();
+      s_last = (atomicAdd(a.counters + p, 1u) == (unsigned)(a.D - 1)) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      finalize_prn<N, T>(a, p, S, s_val, s_idx);
+    }
+    return;
+  }
+  if (j >= 32) return;
+  unsigned last = 0;
+  if (j == 0) {
+    __threadfence();
+    last = (atomicAdd(a.counters + p, 1u) == (unsigned)(a.D - 1)) ? 1u : 0u;
+  }
+  if (__shfl_sync(0xffffffffu, last, 0)) {
+    __threadfence();
+    finalize_prn<N, 32>(a, p, S, s_val, s_idx);
+  }
+}
+
+// Grid: two CTAs per (PRN, Doppler) tile, CTA 2 t + h in cluster t.
+template <bool HALF>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SplitCfg::T, 1) k_xcorr_split(const XcorrArgs a) {
+  extern __shared__ __align__(16) float2 sm[];
+  xcorr_tile_split<HALF>(a, (int)(blockIdx.x >> 1), sm);
+}
+
+template <bool HALF>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(SplitCfg::T, 1)
+    k_xcorr_split_batch(const BatchReq* __restrict__ reqs, const uint32_t* __restrict__ base, int n) {
+  extern __shared__ __align__(16) float2 sm[];
+  const unsigned tile = blockIdx.x >> 1;
+  const int r = find_request(base, n, tile);
+  xcorr_tile_split<HALF>(reqs[r].xc, (int)(tile - __ldg(base + r)), sm);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 bool supported_fft_size(int N) {
@@ -918,7 +1130,7 @@ static int g_xcorr_e[128][15];
 
 int xcorr_default_e(int N) {
   if (N == 4096 || N == 8192) return 16 | (int)GNSS_TUNE_CLASS_LOCAL;
-  return N >= 16384 ? 32 : 16;
+  return N >= 16384 ? 32 | (int)GNSS_TUNE_CLASS_LOCAL : 16;
 }
 
 static bool stage_fits(int N) {
@@ -937,6 +1149,7 @@ static bool stage_fits(int N) {
 bool xcorr_valid_e(int N, int code) {
   if (code == (16 | (int)GNSS_TUNE_STAGED)) return N / 16 <= 1024 && stage_fits(N);
   if (code == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return N == 4096 || N == 8192;
+  if (code == (32 | (int)GNSS_TUNE_CLASS_LOCAL)) return N == 16384;
   return (code == 16 && N / 16 <= 1024) || (code == 32 && N >= 1024) || (code == 8 && N / 8 <= 1024);
 }
 
@@ -986,6 +1199,18 @@ static cudaError_t xcorr_n(const AcqShape& s, const XcorrArgs& a, cudaStream_t s
   }
   if constexpr (N == 4096 || N == 8192) {
     if (v == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return xcorr_ne<N, 16, false, true>(s, a, stream);
+  }
+  if constexpr (N == 16384) {
+    if (v == (32 | (int)GNSS_TUNE_CLASS_LOCAL)) {
+      const unsigned grid = 2u * (unsigned)(s.P * s.D);
+      cudaError_t e;
+      if (s.sets == 2) {
+        if ((e = set_smem(k_xcorr_split<true>, SplitCfg::smem)) != cudaSuccess) return e;
+        return launch_dependent(k_xcorr_split<true>, grid, SplitCfg::T, SplitCfg::smem, stream, a);
+      }
+      if ((e = set_smem(k_xcorr_split<false>, SplitCfg::smem)) != cudaSuccess) return e;
+      return launch_dependent(k_xcorr_split<false>, grid, SplitCfg::T, SplitCfg::smem, stream, a);
+    }
   }
   return xcorr_ne<N, 16, false>(s, a, stream);
 }
@@ -1089,6 +1314,19 @@ static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
   }
   if constexpr (N == 4096 || N == 8192) {
     if (v == (16 | (int)GNSS_TUNE_CLASS_LOCAL)) return xcorr_batch_ne<N, 16, false, true>(g, stream);
+  }
+  if constexpr (N == 16384) {
+    if (v == (32 | (int)GNSS_TUNE_CLASS_LOCAL)) {
+      const unsigned grid = 2u * g.xc_ctas;
+      if (g.sets == 2) {
+        if ((e = set_smem(k_xcorr_split_batch<true>, SplitCfg::smem)) != cudaSuccess) return e;
+        return launch_dependent(k_xcorr_split_batch<true>, grid, SplitCfg::T, SplitCfg::smem, stream, g.reqs,
+                                g.xc_base, g.n);
+      }
+      if ((e = set_smem(k_xcorr_split_batch<false>, SplitCfg::smem)) != cudaSuccess) return e;
+      return launch_dependent(k_xcorr_split_batch<false>, grid, SplitCfg::T, SplitCfg::smem, stream, g.reqs,
+                              g.xc_base, g.n);
+    }
   }
   return xcorr_batch_ne<N, 16, false>(g, stream);
 }

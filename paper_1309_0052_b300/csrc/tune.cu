@@ -26,11 +26,13 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
   gnss_tune_result res;
   memset(&res, 0, sizeof(res));
   res.N = (uint32_t)N;
-  const int cand[5] = {16, 32, 16 | (int)GNSS_TUNE_STAGED, 8, 16 | (int)GNSS_TUNE_CLASS_LOCAL};
+  const int cand[6] = {16, 32, 16 | (int)GNSS_TUNE_STAGED, 8, 16 | (int)GNSS_TUNE_CLASS_LOCAL,
+                       32 | (int)GNSS_TUNE_CLASS_LOCAL};
   if (force_elems) {
     if (!xcorr_valid_e(N, (int)force_elems))
       return fail_status(GNSS_EINVAL, "variant must be 8 (N <= 8192), 16 (N <= 16384), 32 (N >= 1024), 16 | GNSS_TUNE_STAGED "
-                                      "(N <= 8192) or 16 | GNSS_TUNE_CLASS_LOCAL (N = 4096 or 8192)");
+                                      "(N <= 8192), 16 | GNSS_TUNE_CLASS_LOCAL (N = 4096 or 8192) or "
+                                      "32 | GNSS_TUNE_CLASS_LOCAL (N = 16384)");
     set_xcorr_variant(N, (int)force_elems);
     res.chosen = force_elems;
     if (out) *out = res;
@@ -67,7 +69,7 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
   const int prev = xcorr_variant(N);
   float best = 0.f;
   int best_e = prev;
-  for (int k = 0; k < 5 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
     const int E = cand[k];
     if (!xcorr_valid_e(N, E)) continue;
     set_xcorr_variant(N, E);

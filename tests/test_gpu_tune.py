@@ -45,11 +45,13 @@ def _valid(N):
         v.append(8)
     if N in (4096, 8192):
         v.append(16 | CLASS_LOCAL)
+    if N == 16384:
+        v.append(32 | CLASS_LOCAL)  # split over a two-CTA cluster
     return v
 
 
 @pytest.mark.parametrize("N,half,B", [(256, True, 3), (2048, False, 4), (4096, True, 5), (8192, True, 4),
-                                      (16384, False, 4)])
+                                      (16384, False, 4), (16384, True, 4)])
 def test_every_shape_matches_oracle(g, N, half, B):
     coh, fmt = 1, siggen.FMT_2BIT_IQ
     raw, n = _recording(N, coh, B, fmt, N)
@@ -59,7 +61,7 @@ def test_every_shape_matches_oracle(g, N, half, B):
     x = oracle.unpack(raw, n, fmt)
     S = oracle.surfaces(x, N * 1000, coh, B, half, prns, dopp[0] + dopp[1] * np.arange(dopp[2]), 8)
     ref = oracle.detect(S, prns)
-    default = 32 if N >= 16384 else (16 | CLASS_LOCAL) if N in (4096, 8192) else 16
+    default = (32 | CLASS_LOCAL) if N >= 16384 else (16 | CLASS_LOCAL) if N in (4096, 8192) else 16
     try:
         for elems in _valid(N):
             assert plan.autotune(elems)["chosen"] == elems
@@ -86,6 +88,9 @@ def test_invalid_shape_rejected(g):
     assert e.value.status == g.EINVAL
     with pytest.raises(g.GnssError) as e:
         big.autotune(16 | CLASS_LOCAL)  # the class-local schedule is built for N = 4096 and 8192
+    assert e.value.status == g.EINVAL
+    with pytest.raises(g.GnssError) as e:
+        g.Plan(8_192_000, 1, 0, 1, 1, prns=[1]).autotune(32 | CLASS_LOCAL)  # the split is for N = 16384
     assert e.value.status == g.EINVAL
 
 
@@ -166,3 +171,57 @@ def test_class_local_matches_two_barrier_schedule(g, make):
     np.testing.assert_array_equal(s0, s1)
     for f in ("prn", "detected", "set", "dopp_bin", "code_phase", "peak", "second", "ratio"):
         np.testing.assert_array_equal(d0[f], d1[f])
+
+
+def test_split_cluster_batch_equals_alone_and_whole_surface(g):
+    """The 16384-point split (two CTAs per tile in a cluster, merging their row
+    statistics through distributed shared memory): a batch of uneven
+    16.384 MHz requests gives each request's single-launch records and
+    surfaces bit for bit, both agree with the 32-per-thread form within
+    1e-6, and with GNSS_SECOND_WHOLE (the other CTA's surface half read by
+    the detecting CTA) the second peak matches that form too."""
+    recs = siggen.batch_requests(3, ms_range=(10, 30), fs_choices=(16_384_000,))
+    try:
+        res = {}
+        for code in (32 | CLASS_LOCAL, 32):
+            items = []
+            for r in recs:
+                p = g.Plan.for_recording(r)
+                p.autotune(code)
+                rr = torch.from_numpy(np.ascontiguousarray(r.raw)).cuda()
+                out = torch.zeros(p.n_prn * 28, dtype=torch.uint8, device="cuda")
+                sf = torch.zeros(p.surface_shape(), dtype=torch.float32, device="cuda")
+                items.append((p, rr, r.n_samples, out, sf))
+            g.acquire_batch(items)
+            torch.cuda.synchronize()
+            batch = [(g.detections_from_bytes(o.cpu().numpy()), sf.cpu().numpy()) for _, _, _, o, sf in items]
+            alone = []
+            for p, rr, n, out, sf in items:
+                o2, s2 = torch.zeros_like(out), torch.zeros_like(sf)
+                p.acquire_device(rr, n, o2, surface=s2)
+                torch.cuda.synchronize()
+                alone.append((g.detections_from_bytes(o2.cpu().numpy()), s2.cpu().numpy()))
+            for (da, sa), (db, sb) in zip(batch, alone):
+                np.testing.assert_array_equal(sa, sb)
+                for f in ("prn", "detected", "set", "dopp_bin", "code_phase", "peak", "second", "ratio"):
+                    np.testing.assert_array_equal(da[f], db[f])
+            res[code] = alone
+        for (da, sa), (db, sb) in zip(res[32 | CLASS_LOCAL], res[32]):
+            assert np.abs(sa - sb).max() <= 1e-6 * np.abs(sb).max()
+            for f in ("prn", "detected", "set", "dopp_bin", "code_phase"):
+                np.testing.assert_array_equal(da[f], db[f])
+            np.testing.assert_allclose(da["second"], db["second"], rtol=1e-5)
+        r = recs[0]
+        whole = {}
+        for code in (32 | CLASS_LOCAL, 32):
+            p = g.Plan.for_recording(r, second_whole=True)
+            p.autotune(code)
+            rr = torch.from_numpy(np.ascontiguousarray(r.raw)).cuda()
+            sf = torch.zeros(p.surface_shape(), dtype=torch.float32, device="cuda")
+            whole[code] = p.acquire(rr, r.n_samples, surface=sf)
+        a, b = whole[32 | CLASS_LOCAL], whole[32]
+        for f in ("prn", "detected", "dopp_bin", "code_phase"):
+            np.testing.assert_array_equal(a[f], b[f])
+        np.testing.assert_allclose(a["second"], b["second"], rtol=1e-5)
+    finally:
+        g.Plan(16_384_000, 1, 0, 1, 1, prns=[1]).autotune(32 | CLASS_LOCAL)  # the default at 16384
