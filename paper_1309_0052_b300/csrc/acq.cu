@@ -873,7 +873,9 @@ struct SplitCfg {
 // One block: thread j forms z_h at k = j + 512 r (the 8192-point input
 // layout; e^{2 pi i k / N} = wj e^{i pi r / 16}, wj = e^{2 pi i j / N}),
 // transforms it and adds |.|^2.  Only the last element of the upper half can
-// wrap around the row (ksh < 16).
+// wrap around the row (ksh < 16).  The replica is real, so its spectrum is
+// Hermitian: conj(C[k + M]) = C[M - k], and a CTA reads only C[0 .. M]
+// (64 KB, resident in L1 beside the exchange buffers) instead of all of C.
 template <int H>
 __device__ __forceinline__ void split_block(const float2* __restrict__ y, int ksh, const float2* __restrict__ cp,
                                             int j, float2* buf, FftTw<8192, 16, true>& tw, float2 wj,
@@ -888,7 +890,7 @@ __device__ __forceinline__ void split_block(const float2* __restrict__ y, int ks
   for (int r = 0; r < 16; ++r) {
     const float2 lo = c_mulconj(__ldcg(ys + T * r), __ldg(cs + T * r));
     const int kb = j + ksh + T * r + M;
-    const float2 hi = c_mulconj(__ldcg(y + (r < 15 || kb < N ? kb : kb - N)), __ldg(cs + T * r + M));
+    const float2 hi = c_mul(__ldcg(y + (r < 15 || kb < N ? kb : kb - N)), __ldg(cp + M - j - T * r));
     if constexpr (H == 0) v[r] = c_add(lo, hi);
     else v[r] = c_mul(c_sub(lo, hi), c_mul(wj, rot32(r)));
   }
