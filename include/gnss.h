@@ -545,7 +545,7 @@ GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
  * first radix-16 pass the transform splits into 16 independent N/16-point
  * transforms, each on half a warp (4096) or a warp (8192), so one CTA
  * barrier per block instead of two or three.  At N = 16384 variant code
- * 32 | GNSS_TUNE_CLASS_LOCAL (the default there) splits each transform by
+ * 32 | GNSS_TUNE_CLASS_LOCAL splits each transform by
  * decimation in time into two 8192-point class-local transforms, run by the
  * two CTAs of a thread-block cluster (one per output parity, 16 elements
  * and 16 sums per thread), which merge their row statistics through

@@ -207,11 +207,18 @@ int spectrum_classes(const gnss_plan_desc& d, const std::vector<int>& group, std
     shift[k] = (int)((f - base[c]) / 1000);
   }
   const int C = (int)key_of_class.size();
+  // correlate tiles run class by class, so that CTAs resident together read
+  // the blocks of few spectrum rows (L2 locality for long recordings)
+  std::vector<int> order;
+  for (int c = 0; c < C; ++c)
+    for (int k = 0; k < D; ++k)
+      if (cls[k] == c) order.push_back(k);
   packed.clear();
   packed.insert(packed.end(), fgroup.begin(), fgroup.end());
   packed.insert(packed.end(), base.begin(), base.end());
   packed.insert(packed.end(), cls.begin(), cls.end());
   packed.insert(packed.end(), shift.begin(), shift.end());
+  packed.insert(packed.end(), order.begin(), order.end());
   return C;
 }
 
@@ -221,6 +228,7 @@ void spectrum_args(const gnss_plan* plan, AcqShape* s) {
   s->cls_base = plan->C ? plan->d_cls + plan->C : nullptr;
   s->bin_cls = plan->C ? plan->d_cls + 2 * plan->C : nullptr;
   s->bin_shift = plan->C ? plan->d_cls + 2 * plan->C + plan->D : nullptr;
+  s->bin_order = plan->C ? plan->d_cls + 2 * plan->C + 2 * plan->D : nullptr;
 }
 
 // Fold groups: the per-millisecond wipe-off factor exp(-j 2 pi (f i mod 1000) / 1000)

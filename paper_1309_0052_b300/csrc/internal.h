@@ -46,6 +46,7 @@ struct AcqShape {
   const int* cls_base;    // [C] frequency (Hz) of each class's spectrum
   const int* bin_cls;     // [D] class of each bin
   const int* bin_shift;   // [D] (f_d - cls_base) / 1000
+  const int* bin_order;   // [D] bins class by class: the order correlate tiles run in
 };
 
 // Kernel arguments of the correlate + detection kernel.
@@ -53,6 +54,7 @@ struct XcorrArgs {
   const float2* Y;        // [D or C][B][N] spectra of the wiped, folded blocks
   const int* bin_cls;     // NULL (row d of Y) or [D] spectrum row of each bin
   const int* bin_shift;   // NULL or [D] circular shift of that row (bins)
+  const int* bin_order;   // NULL (tiles bin by bin) or [D] bin of each tile row
   const float2* cspec;    // [P][N] code spectra
   int B, D, P, excl;
   float* surface;         // NULL or [sets][P][D][N]
@@ -201,7 +203,7 @@ struct gnss_plan {
   int* d_gkey;        // [G] f mod 1000 of each group (0 when coh_ms == 1)
   int* d_prn_index;   // [33] plan index of PRN 1..32, -1 when not searched
   int C;              // spectrum classes (0 with GNSS_CODE_DOPPLER: one per bin)
-  int* d_cls;         // [2 C + 2 D]: fold group [C], base Hz [C], class [D], shift [D]
+  int* d_cls;         // [2 C + 3 D]: fold group [C], base Hz [C], class [D], shift [D], tile order [D]
   int8_t* d_codes;    // [P][1023] +-1 chips
   float2* d_cspec;    // [P][N] FFT of the sampled replica
 };

@@ -61,7 +61,7 @@ def test_every_shape_matches_oracle(g, N, half, B):
     x = oracle.unpack(raw, n, fmt)
     S = oracle.surfaces(x, N * 1000, coh, B, half, prns, dopp[0] + dopp[1] * np.arange(dopp[2]), 8)
     ref = oracle.detect(S, prns)
-    default = (32 | CLASS_LOCAL) if N >= 16384 else (16 | CLASS_LOCAL) if N in (4096, 8192) else 16
+    default = 32 if N >= 16384 else (16 | CLASS_LOCAL) if N in (4096, 8192) else 16
     try:
         for elems in _valid(N):
             assert plan.autotune(elems)["chosen"] == elems
@@ -224,4 +224,4 @@ def test_split_cluster_batch_equals_alone_and_whole_surface(g):
             np.testing.assert_array_equal(a[f], b[f])
         np.testing.assert_allclose(a["second"], b["second"], rtol=1e-5)
     finally:
-        g.Plan(16_384_000, 1, 0, 1, 1, prns=[1]).autotune(32 | CLASS_LOCAL)  # the default at 16384
+        g.Plan(16_384_000, 1, 0, 1, 1, prns=[1]).autotune(32)  # the default at 16384
