@@ -188,10 +188,13 @@ def make_workloads(args):
     return rec, batch, serve, long_rec, ref_rec, trk_rec
 
 
-def run_batch(g, torch, batch, stream, flush, steps):
+def run_batch(g, torch, batch, stream, flush, steps, peak_tflops):
     """256 uneven recordings: one gnss_acquire_batch per step, one replay of
     the same batch captured into a CUDA graph (gnss_batch_graph_*), and one
-    gnss_acquire_device per recording; recordings resident on the device."""
+    gnss_acquire_device per recording; recordings resident on the device.
+    fp32_frac: the batch's algorithmic FLOPs (wipe + fold + forward FFT per
+    Doppler bin and block, correlate per PRN as well) over the time, against
+    the derived FP32 peak."""
     plans = {}
     items = []
     for r in batch:
@@ -203,6 +206,7 @@ def run_batch(g, torch, batch, stream, flush, steps):
         out = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
         items.append((plan, raw, r.n_samples, out, None))
     cells = sum(_cells(p.n_prn, p.n_dopp, p.N, p.n_blocks(n), p.desc.coh_ms) for p, _, n, _, _ in items)
+    flops = sum(_flops_total(p.n_prn, p.n_dopp, p.n_blocks(n), p.N, p.desc.coh_ms) for p, _, n, _, _ in items)
 
     def batched():
         g.acquire_batch(items, stream=stream)
@@ -232,12 +236,14 @@ def run_batch(g, torch, batch, stream, flush, steps):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         t = statistics.median(ms)
-        res[name] = {"ms_per_batch": t, "cells_per_s": cells / (t * 1e-3), "requests_per_s": len(items) / (t * 1e-3)}
+        res[name] = {"ms_per_batch": t, "cells_per_s": cells / (t * 1e-3), "requests_per_s": len(items) / (t * 1e-3),
+                     "fp32_frac": flops / (t * 1e-3) / 1e12 / peak_tflops}
     graph.close()
     res["speedup"] = res["one_request_per_launch"]["ms_per_batch"] / res["batched"]["ms_per_batch"]
     res["graph_speedup"] = res["one_request_per_launch"]["ms_per_batch"] / res["graph"]["ms_per_batch"]
     res["requests"] = len(items)
     res["cells_per_batch"] = cells
+    res["gflop_per_batch"] = flops / 1e9
     res["workload"] = ("uneven recordings 20-200 ms, fs {2.048, 4.096, 8.192} MHz, 2-bit, 32 PRN, "
                        "+-10 kHz at 250/500 Hz, coherent 500/step ms, all blocks")
     return res
@@ -663,7 +669,7 @@ def run_ours(args):
     if trk_rec is not None:
         line["track"] = run_track(g, torch, trk_rec, stream, steps=3)
     if batch:
-        line["batch"] = run_batch(g, torch, batch, stream, flush, steps=3)
+        line["batch"] = run_batch(g, torch, batch, stream, flush, steps=3, peak_tflops=peak_tflops)
     if serve:
         line["serving"] = [run_serving(g, serve, float(r), args.serve_seconds)
                            for r in args.serve_rates.split(",") if r.strip()]
