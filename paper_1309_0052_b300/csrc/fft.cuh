@@ -238,18 +238,32 @@ template <int N, int E, int R, int NS, bool INV>
 __device__ __forceinline__ void pass_compute(float2 (&v)[E], int j) {
   constexpr int T = N / E;
   constexpr int Q = E / R;
+  // Twiddle base W^k, k = (j + T q) mod NS, of each butterfly q.  T and NS
+  // are powers of two: if NS <= T every q has k = j mod NS; otherwise
+  // k = j + T (q mod NS/T), and W^k = W^j W^(T m) with W^(T m) a constant of
+  // the pass.  One sincospif per pass and thread, then constant products.
+  constexpr float scale = (INV ? 2.f : -2.f) / float(NS * R);
+  float2 w0 = make_float2(1.f, 0.f);
+  if constexpr (NS > 1) {
+    float sn, cs;
+    sincospif(scale * float(j & (NS - 1)), &sn, &cs);
+    w0 = make_float2(cs, sn);
+  }
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     float2 u[R];
 #pragma unroll
     for (int s = 0; s < R; ++s) u[s] = v[q + Q * s];
     if constexpr (NS > 1) {
-      const int J = j + T * q;
-      const int k = J & (NS - 1);
-      constexpr float scale = (INV ? 2.f : -2.f) / float(NS * R);
-      float sn, cs;
-      sincospif(scale * float(k), &sn, &cs);
-      const float2 w = make_float2(cs, sn);
+      float2 w = w0;
+      if constexpr (NS > T) {
+        const int m = q % (NS / T);
+        if (m != 0) {
+          float sn, cs;
+          sincospif(scale * float(T * m), &sn, &cs);  // a constant of the pass
+          w = c_mul(w0, make_float2(cs, sn));
+        }
+      }
       if constexpr (R == 16) {
         const float2 w2 = c_mul(w, w), w4 = c_mul(w2, w2), w8 = c_mul(w4, w4);
         dft16_tw<INV>(u, w, w2, w4, w8);
