@@ -123,6 +123,34 @@ def test_acquire_weak_100ms_full_size_parity(g):
     np.testing.assert_array_equal(det2, det)
 
 
+def test_class_by_class_tile_order_large_spectra(g):
+    """Spectra above the L2 budget (24 MB) switch the correlate tiles to the
+    class-by-class order: 60 ms at 16.384 MHz, 1 ms blocks, 81 bins of 250 Hz
+    (8 spectrum classes, 63 MB of spectra), three PRNs; surfaces and
+    detections against the oracle, and every (PRN, bin) row lands in its own
+    place.  The same recording cut to 20 ms (21 MB, the bin-by-bin order)
+    agrees too."""
+    N, fs = 16384, 16_384_000
+    prns = [3, 9, 30]
+    dopp = np.arange(81) * 250 - 10000
+    rng = np.random.default_rng(77)
+    sats = [siggen.Sat(prn=9, cn0_dbhz=48.0, dopp_hz=-1750.0, code_phase_chips=100.7, carrier_phase=0.3,
+                       bit_edge_ms=3.0),
+            siggen.Sat(prn=30, cn0_dbhz=46.0, dopp_hz=3260.0, code_phase_chips=611.2, carrier_phase=1.1,
+                       bit_edge_ms=9.0)]
+    for ms in (60, 20):
+        n = ms * N
+        x = siggen.synthesize(rng, fs, n, sats)
+        li, lq = siggen.quantize_2bit(x, sats, fs)
+        raw = siggen.pack(li, lq, siggen.FMT_2BIT_IQ)
+        plan = g.Plan(fs, 1, -10000, 250, 81, prns=prns, fmt=siggen.FMT_2BIT_IQ)
+        det, S = _gpu_acquire(plan, raw, n)
+        dref, Sref = _oracle(dict(fmt=siggen.FMT_2BIT_IQ, fs=fs, coh=1, dopp=dopp), raw, n, prns, ms)
+        compare_surfaces(S, Sref)
+        assert compare_detections(det, dref, Sref) == 0
+        assert {int(d["prn"]) for d in det if d["detected"]} == {9, 30}
+
+
 def test_host_device_and_async_paths_agree(g):
     rec = siggen.plain_4ms()
     plan = g.Plan.for_recording(rec)
