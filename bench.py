@@ -407,6 +407,44 @@ def run_zoom(g, torch, rec, stream, steps):
                            "zoom": float(fine["ratio"].mean()) if len(fine) else None}}
 
 
+def run_fft_sizes(g, torch, stream, flush, steps, peak_tflops, sizes=(2048, 4096, 8192, 16384)):
+    """The correlate kernel at each FFT size on a 100 ms 2-bit recording at
+    fs = N kHz (one satellite at 45 dB-Hz), 32 PRNs x 81 Doppler bins of 250 Hz,
+    1 ms coherent blocks, in the default launch shape of that size: launch time
+    from the traced entry point's events (L2 flushed before each step) and the
+    fraction of the derived FP32 peak under the 5 N log2 N convention."""
+    import siggen
+    res = {}
+    for N in sizes:
+        fs, n = N * 1000, 100 * N
+        rng = np.random.default_rng(1309005210 + N)
+        sats = [siggen.Sat(prn=9, cn0_dbhz=45.0, dopp_hz=-1750.0, code_phase_chips=100.7, carrier_phase=0.3,
+                           bit_edge_ms=3.0)]
+        x = siggen.synthesize(rng, fs, n, sats)
+        li, lq = siggen.quantize_2bit(x, sats, fs)
+        raw = torch.from_numpy(np.ascontiguousarray(siggen.pack(li, lq, siggen.FMT_2BIT_IQ))).cuda()
+        plan = g.Plan(fs, 1, -10000, 250, 81, prns=range(1, 33), fmt=siggen.FMT_2BIT_IQ)
+        out = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                plan.acquire_device(raw, n, out, stream=stream)
+        torch.cuda.synchronize()
+        tev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.fill_(float(k))
+                plan.acquire_device_traced(raw, n, out, tev[k], stream=stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(e[2].elapsed_time(e[3]) for e in tev)
+        B = plan.n_blocks(n)
+        fl = _flops_xcorr(plan.n_prn, plan.n_dopp, B, N)
+        res[str(N)] = {"correlate_ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+                       "frac": fl / (ms * 1e-3) / 1e12 / peak_tflops}
+        plan.close()
+    return {"workload": "100 ms at fs = N kHz, 2-bit, 32 PRN x 81 Doppler (250 Hz), 1 ms coherent x 100",
+            "sizes": res}
+
+
 def run_serving(g, serve, rate, seconds, seed=1309005205):
     """Poisson arrivals at 'rate' requests/s for 'seconds' through
     gnss_submit / gnss_poll; latency = submit -> result observed (host clock)."""
@@ -664,6 +702,8 @@ def run_ours(args):
         line["code_doppler"] = run_code_doppler(g, torch, long_rec, stream, flush, steps=10)
     if not args.no_zoom:
         line["zoom"] = run_zoom(g, torch, rec, stream, steps=10)
+    if not args.no_sizes:
+        line["fft_sizes"] = run_fft_sizes(g, torch, stream, flush, steps=5, peak_tflops=peak_tflops)
     if ref_rec is not None:
         line["refine"] = run_refine(g, torch, ref_rec, stream, steps=10)
     if trk_rec is not None:
@@ -834,6 +874,7 @@ def main():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-track", action="store_true")
     ap.add_argument("--no-zoom", action="store_true")
+    ap.add_argument("--no-sizes", action="store_true", help="skip the correlate at N = 2048 ... 16384")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-rates", default="50,100,200",
                     help="offered Poisson arrival rates (requests/s), one serving run each")
