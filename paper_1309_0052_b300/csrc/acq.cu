@@ -94,7 +94,13 @@ struct XCfg {
       sizeof(float2) * (CL ? ClassLocal<(CL ? N : 4096)>::smem_elems : FftShape<N>::smem_elems);
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
   static constexpr size_t stage_off = (DB || CL ? 2 : 1) * buf_bytes;
-  static constexpr size_t smem = stage_off + (ST ? sizeof(float2) * N : 0);
+  // At 16384 with 32 per thread, sums 16-31 of each thread live in
+  // thread-private shared memory (slot (r - 16) T + j): 32 data and 32 sum
+  // registers do not fit 128 with the passes' temporaries, and the spills
+  // cost more L1 traffic than these slots.
+  static constexpr bool SHACC = N == 16384 && E == 32 && !CL && !ST;
+  static constexpr size_t sacc_off = stage_off + (ST ? sizeof(float2) * N : 0);
+  static constexpr size_t smem = sacc_off + (SHACC ? sizeof(float) * 16 * T : 0);
   // CTAs per SM the registers must allow: a budget of 128 registers per
   // thread (two 256-thread CTAs, four of 128, ...; registers are allocated
   // per warp, so CTAs under 32 threads count as one warp), 64 at 512 threads
@@ -616,6 +622,7 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh
                                            float (&acc)[E], const StageIssue& next, uint32_t& parity,
                                            bool& stage_ok) {
   constexpr int T = N / E;
+  constexpr bool SHACC = XCfg<N, E, ST, CL>::SHACC;
   const int js = j + ksh;  // element k of the bin's spectrum is element k + ksh of the row
   if constexpr (TWC) tw.launder();
   // Re-read the code spectrum from L1 every block: hoisting these 16 loads
@@ -651,8 +658,16 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh
       fft_block<N, E, true, DB>(v, j, buf0, buf1, phase);
     }
   }
+  if constexpr (SHACC) {
+    float* sacc = reinterpret_cast<float*>(reinterpret_cast<char*>(buf0) + XCfg<N, E, ST, CL>::sacc_off) + j;
 #pragma unroll
-  for (int r = 0; r < E; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
+    for (int r = 0; r < 16; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
+#pragma unroll
+    for (int r = 16; r < E; ++r) sacc[(r - 16) * T] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, sacc[(r - 16) * T]));
+  } else {
+#pragma unroll
+    for (int r = 0; r < E; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
+  }
 }
 
 // Per-PRN detection, run by the last CTA to finish a PRN (all its threads):
@@ -756,6 +771,11 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
     float acc[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) acc[r] = 0.f;
+    float* const sacc = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + X::sacc_off) + j;
+    if constexpr (X::SHACC) {
+#pragma unroll
+      for (int r = 16; r < E; ++r) sacc[(r - 16) * T] = 0.f;  // this thread's own slots
+    }
     for (int b = set; b < a.B; b += S) {
       if constexpr (ST) {
         // the block after b: the next of this set, else the first of the next set
@@ -765,6 +785,10 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
       }
       corr_block<N, E, DB, TWC, ST, CL>(yd + (size_t)b * N, ksh, cp, j, buf0, buf1, phase, tw, acc, next,
                                         parity, stage_ok);
+    }
+    if constexpr (X::SHACC) {
+#pragma unroll
+      for (int r = 16; r < E; ++r) acc[r] = sacc[(r - 16) * T];
     }
     // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
     constexpr float sc = 1.f / ((float)N * (float)N);
