@@ -94,13 +94,14 @@ struct XCfg {
       sizeof(float2) * (CL ? ClassLocal<(CL ? N : 4096)>::smem_elems : FftShape<N>::smem_elems);
   static constexpr bool DB = 2 * buf_bytes <= 160 * 1024;     // ping-pong exchange buffers
   static constexpr size_t stage_off = (DB || CL ? 2 : 1) * buf_bytes;
-  // At 16384 with 32 per thread, sums 16-31 of each thread live in
-  // thread-private shared memory (slot (r - 16) T + j): 32 data and 32 sum
-  // registers do not fit 128 with the passes' temporaries, and the spills
-  // cost more L1 traffic than these slots.
+  // At 16384 with 32 per thread, sums 8-31 of each thread live in
+  // thread-private shared memory (slot (r - 8) T + j, 48 KB): 32 data and 32
+  // sum registers do not fit 128 with the passes' temporaries, and the
+  // spills cost more than these slots (measured: 8 sums in registers beat
+  // 4, 12, 16 and none).
   static constexpr bool SHACC = N == 16384 && E == 32 && !CL && !ST;
   static constexpr size_t sacc_off = stage_off + (ST ? sizeof(float2) * N : 0);
-  static constexpr size_t smem = sacc_off + (SHACC ? sizeof(float) * 16 * T : 0);
+  static constexpr size_t smem = sacc_off + (SHACC ? sizeof(float) * (E - 8) * T : 0);
   // CTAs per SM the registers must allow: a budget of 128 registers per
   // thread (two 256-thread CTAs, four of 128, ...; registers are allocated
   // per warp, so CTAs under 32 threads count as one warp), 64 at 512 threads
@@ -661,9 +662,9 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh
   if constexpr (SHACC) {
     float* sacc = reinterpret_cast<float*>(reinterpret_cast<char*>(buf0) + XCfg<N, E, ST, CL>::sacc_off) + j;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
+    for (int r = 0; r < 8; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
 #pragma unroll
-    for (int r = 16; r < E; ++r) sacc[(r - 16) * T] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, sacc[(r - 16) * T]));
+    for (int r = 8; r < E; ++r) sacc[(r - 8) * T] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, sacc[(r - 8) * T]));
   } else {
 #pragma unroll
     for (int r = 0; r < E; ++r) acc[r] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, acc[r]));
@@ -774,7 +775,7 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
     float* const sacc = reinterpret_cast<float*>(reinterpret_cast<char*>(sm) + X::sacc_off) + j;
     if constexpr (X::SHACC) {
 #pragma unroll
-      for (int r = 16; r < E; ++r) sacc[(r - 16) * T] = 0.f;  // this thread's own slots
+      for (int r = 8; r < E; ++r) sacc[(r - 8) * T] = 0.f;  // this thread's own slots
     }
     for (int b = set; b < a.B; b += S) {
       if constexpr (ST) {
@@ -788,7 +789,7 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
     }
     if constexpr (X::SHACC) {
 #pragma unroll
-      for (int r = 16; r < E; ++r) acc[r] = sacc[(r - 16) * T];
+      for (int r = 8; r < E; ++r) acc[r] = sacc[(r - 8) * T];
     }
     // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
     constexpr float sc = 1.f / ((float)N * (float)N);
