@@ -156,6 +156,7 @@ struct RefineJob {
   int N;                   // samples per ms
   int L;                   // samples in the coherent window (from the recording start)
   double fs;
+  double inv_fs;           // 1 / fs
   const int8_t* codes;     // [P][1023] +-1
   const int* prn_index;    // [33] plan index of PRN 1..32 (-1 = not in the plan)
 };

@@ -97,33 +97,64 @@ struct CodeBits {
   float scale;  // 1, or 0 when the PRN is not in the plan (P and gradient 0)
 };
 
+// This thread's share of the window (fixed for the CTA): samples
+// [n0, n0 + chunk), and the code position of n0, n0 * 1023 = q0 N + rem0.
+struct Span {
+  int n0, chunk, q0, rem0;
+  __device__ __forceinline__ Span(const RefineJob& J, int T) {
+    const int groups = J.L / 8;
+    const int gpt = (groups + T - 1) / T;
+    const int g_end = min(groups, ((int)threadIdx.x + 1) * gpt);
+    chunk = max(0, g_end - (int)threadIdx.x * gpt) * 8;
+    n0 = min((int)threadIdx.x * gpt, groups) * 8;
+    const long long prod = (long long)n0 * 1023;
+    q0 = (int)(prod / J.N);
+    rem0 = (int)(prod - (long long)q0 * J.N);
+  }
+};
+
+// Quantities of one evaluation that are the same for every thread, formed by
+// thread 0 in FP64 (which runs at a small fraction of the FP32 rate) and
+// read by all after a CTA barrier.
+struct EvalPoint {
+  uint64_t s_fx;  // cycles per sample s = frac(f / fs), times 2^64
+  float2 rot;     // e^{-j 2 pi s}
+  int ti;         // code delay: integer part (tau modulo 1023)
+  float tf;       // and its fraction + 1/2, in [0.5, 1.5)
+};
+
 template <int T, int FMT, bool GRAD>
-__device__ EvalOut evaluate(const RefineJob& J, const CodeBits& cb, double f, double tau, float* red) {
-  const int groups = J.L / 8;
-  const int gpt = (groups + T - 1) / T;
-  const int g_end = min(groups, ((int)threadIdx.x + 1) * gpt);
-  const int chunk = max(0, g_end - (int)threadIdx.x * gpt) * 8;
-  const int n0 = min((int)threadIdx.x * gpt, groups) * 8;
-  // carrier e^{-j 2 pi f n / fs}: phase of n0 in double, then per-sample rotation
-  const double cyc0 = f * (double)n0 / J.fs;
-  const float ph0 = (float)(cyc0 - floor(cyc0));
+__device__ EvalOut evaluate(const RefineJob& J, const CodeBits& cb, const Span& sp, double f, double tau, float* red,
+                            EvalPoint* pt) {
+  if (threadIdx.x == 0) {
+    // carrier e^{-j 2 pi f n / fs}: the phase of sample n0 is frac(n0 s), an
+    // exact integer product modulo one cycle in 64-bit fixed point
+    const double step_cyc = f * J.inv_fs;
+    const double s_frac = step_cyc - floor(step_cyc);  // [0, 1)
+    pt->s_fx = (uint64_t)(s_frac * 18446744073709551616.0);
+    float ss, sc;
+    sincospif((float)(-2.0 * s_frac), &ss, &sc);
+    pt->rot = make_float2(sc, ss);
+    // P has period 1023 chips in tau: wrap it so the integer part stays small
+    const double tw = tau - 1023.0 * floor(tau * (1.0 / 1023.0));
+    const double tfl = floor(tw);
+    pt->ti = (int)tfl;
+    pt->tf = (float)(tw - tfl) + 0.5f;
+  }
+  __syncthreads();  // the previous evaluation's readers passed its reduction barrier
+  const int n0 = sp.n0, chunk = sp.chunk;
+  const uint64_t ph_fx = (uint64_t)n0 * pt->s_fx;  // n0 s modulo 1, times 2^64
+  const float ph0 = (float)(uint32_t)(ph_fx >> 40) * 0x1p-24f;
   float s0, c0;
   sincospif(-2.f * ph0, &s0, &c0);
-  const double step_cyc = f / J.fs;
-  float ss, sc;
-  sincospif((float)(-2.0 * (step_cyc - floor(step_cyc))), &ss, &sc);
   float2 car = make_float2(c0, s0);
-  const float2 rot = make_float2(sc, ss);
+  const float2 rot = pt->rot;
   // code position: n * 1023 = q N + rem; u = (q - ti) + (rem / N - tf - 1/2)
-  // P has period 1023 chips in tau: wrap it so the integer part stays small
-  const double tw = tau - 1023.0 * floor(tau / 1023.0);
-  const double tfl = floor(tw);
-  const int ti = (int)tfl;
-  const float tf = (float)(tw - tfl) + 0.5f;  // in [0.5, 1.5)
+  const int ti = pt->ti;
+  const float tf = pt->tf;
   const float invN = 1.f / (float)J.N;
-  long long prod = (long long)n0 * 1023;
-  int q = (int)(prod / J.N);
-  int rem = (int)(prod - (long long)q * J.N);
+  int q = sp.q0;
+  int rem = sp.rem0;
   const float half_L = 0.5f * (float)J.L;
   float zr = 0.f, zi = 0.f, fr = 0.f, fi = 0.f, tr = 0.f, tii = 0.f;
   for (int base = 0; base < chunk; base += 8) {
@@ -195,7 +226,7 @@ __device__ EvalOut evaluate(const RefineJob& J, const CodeBits& cb, double f, do
   o.gf = o.gt = 0.f;
   if constexpr (GRAD) {
     // dz/df -> (-j 2 pi / fs) sum (n - L/2) w ctilde = (2 pi / fs) (fi - j fr)
-    const float g = (float)(2.0 * 3.14159265358979323846 / J.fs);
+    const float g = (float)(2.0 * 3.14159265358979323846 * J.inv_fs);
     const float dfr = g * fi, dfi = -g * fr;
     o.gf = 2.f * (zr * dfr + zi * dfi);
     o.gt = 2.f * (zr * tr + zi * tii);
@@ -225,7 +256,9 @@ __global__ void __launch_bounds__(T) k_refine_eval(RefineJob J, const int* __res
   __shared__ CodeBits chips;
   __shared__ float red[32 * 6];
   load_chips<T>(J, prn[blockIdx.x], chips);
-  const EvalOut o = evaluate<T, FMT, true>(J, chips, f[blockIdx.x], tau[blockIdx.x], red);
+  __shared__ EvalPoint pt;
+  const Span sp(J, T);
+  const EvalOut o = evaluate<T, FMT, true>(J, chips, sp, f[blockIdx.x], tau[blockIdx.x], red, &pt);
   if (threadIdx.x == 0) {
     P[blockIdx.x] = o.P;
     if (dPdf) dPdf[blockIdx.x] = o.gf;
@@ -260,6 +293,8 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
   __shared__ float red[32 * 6];
   const gnss_candidate c = cands[blockIdx.x];
   load_chips<T>(J, c.prn, chips);
+  __shared__ EvalPoint pt;
+  const Span sp(J, T);
   const double c1 = 1e-4, tol_tau = 1e-5, tol_f = 1e-3;
   const double Tw = (double)J.L / J.fs;
   const double curv = (2.0 * 3.14159265358979323846) * (2.0 * 3.14159265358979323846) * Tw * Tw / 6.0;
@@ -267,18 +302,18 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
   if (search_hz > 0.0) {
     const double d = J.fs / (2.0 * (double)J.L);
     const int K = (int)floor(search_hz / d);
-    float best = evaluate<T, FMT, false>(J, chips, c.f_hz, tau, red).P;
+    float best = evaluate<T, FMT, false>(J, chips, sp, c.f_hz, tau, red, &pt).P;
     for (int k = 1; k <= K; ++k)
       for (int sg = -1; sg <= 1; sg += 2) {
         const double fk = c.f_hz + sg * k * d;
-        const float Pk = evaluate<T, FMT, false>(J, chips, fk, tau, red).P;
+        const float Pk = evaluate<T, FMT, false>(J, chips, sp, fk, tau, red, &pt).P;
         if (Pk > best) {
           best = Pk;
           f = fk;
         }
       }
   }
-  EvalOut e = evaluate<T, FMT, true>(J, chips, f, tau, red);
+  EvalOut e = evaluate<T, FMT, true>(J, chips, sp, f, tau, red, &pt);
   int it = 0, status = 2;
   for (; it < max_iter; ++it) {
     double move_f = 0.0, move_t = 0.0;
@@ -286,7 +321,7 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
     if (df != 0.0) {
       double alpha = 1.0;
       for (int h = 0; h <= 20; ++h) {
-        const EvalOut en = evaluate<T, FMT, true>(J, chips, f + alpha * df, tau, red);
+        const EvalOut en = evaluate<T, FMT, true>(J, chips, sp, f + alpha * df, tau, red, &pt);
         const bool armijo = (double)en.P >= (double)e.P + c1 * alpha * (double)e.gf * df;
         const bool flatter = fabsf(en.gf) < fabsf(e.gf) && (double)en.P >= (1.0 - 1e-5) * (double)e.P;
         if (armijo || flatter) {
@@ -305,12 +340,12 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
       double alpha = 1.0;
       bool accepted = false;
       for (int h = 0; h <= 20; ++h) {
-        const EvalOut en = evaluate<T, FMT, false>(J, chips, f, tau + alpha * dt, red);
+        const EvalOut en = evaluate<T, FMT, false>(J, chips, sp, f, tau + alpha * dt, red, &pt);
         if ((double)en.P >= (double)e.P + c1 * alpha * (double)e.gt * dt) {
           tau += alpha * dt;
           s_tau *= alpha;
           move_t = fabs(alpha * dt);
-          e = evaluate<T, FMT, true>(J, chips, f, tau, red);
+          e = evaluate<T, FMT, true>(J, chips, sp, f, tau, red, &pt);
           accepted = true;
           break;
         }
@@ -319,12 +354,12 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
       if (!accepted) {  // a segment slope is one-sided at an exact kink: try the other direction
         alpha = 1.0;
         for (int h = 0; h <= 20; ++h) {
-          const EvalOut en = evaluate<T, FMT, false>(J, chips, f, tau - alpha * dt, red);
+          const EvalOut en = evaluate<T, FMT, false>(J, chips, sp, f, tau - alpha * dt, red, &pt);
           if (en.P > e.P) {
             tau -= alpha * dt;
             s_tau *= alpha;
             move_t = fabs(alpha * dt);
-            e = evaluate<T, FMT, true>(J, chips, f, tau, red);
+            e = evaluate<T, FMT, true>(J, chips, sp, f, tau, red, &pt);
             accepted = true;
             break;
           }
@@ -401,6 +436,7 @@ static gnss_status refine_job(const gnss_plan* plan, const void* samples_dev, si
   J->N = plan->N;
   J->L = (int)L;
   J->fs = (double)plan->desc.fs_hz;
+  J->inv_fs = 1.0 / J->fs;
   J->codes = plan->d_codes;
   J->prn_index = plan->d_prn_index;
   return GNSS_OK;
