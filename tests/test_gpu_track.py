@@ -68,17 +68,22 @@ def test_track_1s_parity_and_lock(g):
         assert np.mean(last["zp"][:, 1] ** 2) < 0.1 * np.mean(last["zp"][:, 0] ** 2)
 
 
-def test_warp_per_channel_launch(g):
-    """With enough channels to fill the GPU (>= 4 per SM) each channel runs
-    on one warp: 80 copies of the 8 satellites' channels give identical
-    records copy to copy, and match the oracle."""
+@pytest.mark.parametrize("tpc", [32, 64, 128, 256])
+def test_threads_per_channel_launch(g, tpc):
+    """Channels take the smallest group of 32 .. 256 threads that gives them
+    together the GPU's resident threads (1024 per SM), so the channel count
+    picks the group: copies of the 8 satellites' channels, as many as select
+    a group of tpc threads, give identical records copy to copy and match the
+    oracle."""
     rec = siggen.track_1s()
     prn, f, tau = siggen.track_starts(rec)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    reps = max(80, -(-4 * sms // len(prn)))
+    # tpc < 256: the fewest channels for which tpc threads each suffice
+    n_chan = 80 * len(prn) if tpc == 256 else -(-sms * 1024 // tpc)
+    reps = -(-n_chan // len(prn))
+    assert tpc == 256 or reps * len(prn) < 2 * n_chan  # still in tpc's range
     n_int = 200
     out = _run(g, rec, np.tile(prn, reps), np.tile(f, reps), np.tile(tau, reps), n_int)
-    assert len(out) >= 4 * sms
     for r in range(1, reps):
         np.testing.assert_array_equal(out[r * len(prn):(r + 1) * len(prn)], out[:len(prn)])
     x = oracle.unpack(rec.raw, rec.n_samples, rec.fmt)
