@@ -866,9 +866,11 @@ __global__ void __launch_bounds__(XCfg<N, E, ST, CL>::T, XCfg<N, E, ST, CL>::MIN
 // so CTA h of the pair (its rank in the cluster) sums |X[2q + h]|^2 with the
 // 8192-point class-local transform: 16 accumulators per thread and no spills,
 // where one 16384-point CTA holds 32 elements and 32 sums per thread.  Each
-// CTA reads both halves of Y and C and forms the products it needs (handing
-// the halves over through distributed shared memory instead took two
-// cluster barriers per block and ran 40% slower).  The pair merges its row
+// CTA reads both halves of Y, and C's lower half (the upper one through its
+// Hermitian symmetry), and forms the products it needs (handing the halves
+// over through distributed shared memory instead took two cluster barriers
+// per block and ran 40% slower).  Offered to the autotuner; the default at
+// 16384 is the 32-per-thread form.  The pair merges its row
 // statistics through distributed shared memory: the row's peak and the
 // smallest phase holding it, then each half's maximum outside the band
 // around that phase.
