@@ -641,7 +641,9 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh
     v[E - 1] = c_mulconj(next.stg[last >= N ? last - N : last], __ldg(cp + j + T * (E - 1)));
     fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw, next);
   } else {
-    // Y streams from L2 (not kept in L1); the code spectrum stays L1-resident.
+    // Y streams from L2 (not kept in L1); the code spectrum goes through the
+    // non-coherent path (measured: it too is served from L2, and loads that
+    // allocate in L1 ran slower, their hits using the data path the exchanges load).
     // ksh < 16 <= T (spectrum classes are cut so): only the last element can wrap
     const float2* ys = y + js;
 #pragma unroll
