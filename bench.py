@@ -438,7 +438,8 @@ def run_fft_sizes(g, torch, stream, flush, steps, peak_tflops, sizes=(2048, 4096
         ms = statistics.mean(e[2].elapsed_time(e[3]) for e in tev)
         B = plan.n_blocks(n)
         fl = _flops_xcorr(plan.n_prn, plan.n_dopp, B, N)
-        res[str(N)] = {"correlate_ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+        res[str(N)] = {"kernel": xcorr_kernel_name(plan.xcorr_variant(), N, half=False),
+                       "correlate_ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
                        "frac": fl / (ms * 1e-3) / 1e12 / peak_tflops}
         plan.close()
     return {"workload": "100 ms at fs = N kHz, 2-bit, 32 PRN x 81 Doppler (250 Hz), 1 ms coherent x 100",
@@ -684,7 +685,8 @@ def run_ours(args):
                 "p50_ms": float(np.percentile(e2e_ms, 50)), "p99_ms": float(np.percentile(e2e_ms, 99))},
         "gpu_launches": 3 * args.steps,
         "stage_ms": stage_ms,
-        "roofline": {"bound": "alu", "kernel": "k_xcorr<4096,16,half-bit,class-local>", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": xcorr_kernel_name(plan.xcorr_variant(), N, half=rec.half_bit),
+                     "variant_code": plan.xcorr_variant(), "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                      "traffic": traffic, "flops_per_launch": x_flops, "launch_ms": x_ms,
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 x max SM clock (of derived)",
@@ -721,10 +723,22 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def xcorr_kernel_name(code, N, half):
+    """Name of the correlate kernel a variant code launches at FFT size N."""
+    e, sets = code & 0xFF, "half-bit" if half else "one set"
+    if code & 0x400:
+        k, m = ((code >> 12) & 3) + 1, ((code >> 14) & 3) + 1
+        form = "3 CTAs/SM" if code & 0x800 else ("%d PRN%s, %d bin%s" % (k, "s" * (k > 1), m, "s" * (m > 1)))
+        return "k_xcorr_tm<%d,%d,%s,%s>" % (N, e, sets, form)
+    if code & 0x200:
+        return ("k_xcorr_split<%s>" % sets) if N == 16384 else "k_xcorr<%d,%d,%s,class-local>" % (N, e, sets)
+    return "k_xcorr<%d,%d,%s%s>" % (N, e, sets, ",staged" if code & 0x100 else "")
+
+
 def _kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("fft.cuh", "acq.cu"):
+    for f in ("fft.cuh", "xcorr.cuh", "acq.cu", "xcorr_tm.cu"):
         with open(os.path.join(ROOT, "paper_1309_0052_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -137,6 +137,8 @@ typedef struct {
   uint32_t n_sets;     /* 1, or 2 with GNSS_HALF_BIT            */
   uint32_t excl;       /* second-peak exclusion half-width, ceil(N/1023) samples */
   uint32_t block_len;  /* L = coh_ms * N samples per block      */
+  uint32_t xcorr_variant; /* correlate-kernel variant code used for N on the
+                             current device now (see gnss_autotune)   */
 } gnss_plan_info;
 
 typedef struct gnss_plan gnss_plan;
@@ -549,23 +551,44 @@ GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
  * decimation in time into two 8192-point class-local transforms, run by the
  * two CTAs of a thread-block cluster (one per output parity, 16 elements
  * and 16 sums per thread), which merge their row statistics through
- * distributed shared memory.  With
- * force_elems = 0 every valid variant is timed on a probe shaped like the
- * plan (its Doppler bins up to 32, its sets, 8 blocks) and the fastest is
- * recorded for the plan's FFT size on the current device; with force_elems
- * = a variant code that variant is recorded without timing (GNSS_EINVAL if
- * it is not valid for N).  Later launches of that FFT size (single, batched,
- * served) use it.  Synchronous.  out may be NULL. */
+ * distributed shared memory.
+ *
+ * GNSS_TUNE_TMEM (N = 2048, 4096, 8192 with 16 per thread, N = 16384 with
+ * 32) keeps the code spectra and the non-coherent sums in the SM's tensor
+ * memory instead of re-reading C_p from L2 every block and holding the sums
+ * in registers; with 16 per thread the freed registers hold the next block's
+ * spectrum, loaded under the current block's transform.  Its CTA shape is
+ * part of the code: GNSS_TUNE_PRNS(k) PRNs per CTA (k = 1 or 2; one spectrum
+ * load feeds k products and transforms; 1 at 16384) and GNSS_TUNE_BINS(m)
+ * Doppler bins per CTA (m = 1 or 2, run one after another with the code
+ * spectra kept).  It gives the register form's surfaces and records bit for
+ * bit.  A shape is valid only where the CTA's tensor-memory columns fit its
+ * share of the register file (so co-resident CTAs never wait for columns).
+ *
+ * With force_elems = 0 every valid variant is timed on a probe shaped like
+ * the plan (its Doppler bins up to 32, its sets, 8 blocks) and the fastest
+ * is recorded for the plan's FFT size on the current device; with
+ * force_elems = a variant code that variant is recorded without timing
+ * (GNSS_EINVAL if it is not valid for N).  Later launches of that FFT size
+ * (single, batched, served) use it.  Synchronous.  out may be NULL. */
 #define GNSS_TUNE_STAGED 0x100u
 #define GNSS_TUNE_CLASS_LOCAL 0x200u
+#define GNSS_TUNE_TMEM 0x400u
+#define GNSS_TUNE_OCC 0x800u /* TMEM variant, one PRN and bin: one more CTA per SM */
+#define GNSS_TUNE_PRNS(k) ((((uint32_t)(k)) - 1u) << 12) /* PRNs per CTA (TMEM variant) */
+#define GNSS_TUNE_BINS(m) ((((uint32_t)(m)) - 1u) << 14) /* Doppler bins per CTA (TMEM variant) */
 typedef struct {
-  uint32_t N;            /* FFT size tuned                                */
-  uint32_t n_variants;   /* variants timed                                */
-  uint32_t elems[8];     /* variant code of each timed variant: elements  */
-                         /* per thread | GNSS_TUNE_STAGED or              */
-                         /* GNSS_TUNE_CLASS_LOCAL                         */
-  float ms[8];           /* median probe time of each (ms)                */
-  uint32_t chosen;       /* variant code now in use for N                 */
+  uint32_t N;             /* FFT size tuned                                 */
+  uint32_t n_variants;    /* variants timed                                 */
+  uint32_t elems[16];     /* variant code of each timed variant: elements   */
+                          /* per thread | GNSS_TUNE_STAGED,                 */
+                          /* GNSS_TUNE_CLASS_LOCAL or GNSS_TUNE_TMEM with   */
+                          /* its GNSS_TUNE_PRNS / GNSS_TUNE_BINS            */
+  float ms[16];           /* median probe time of each (ms)                 */
+  uint32_t chosen;        /* variant code now in use for N                  */
+  uint32_t prns_per_cta;  /* PRNs one correlate CTA takes under 'chosen'    */
+  uint32_t bins_per_cta;  /* Doppler bins one correlate CTA takes           */
+  uint32_t reserved;
 } gnss_tune_result;
 
 GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_elems, gnss_tune_result* out);

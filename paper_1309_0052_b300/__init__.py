@@ -50,13 +50,14 @@ class ServerStats(C.Structure):
 
 
 class TuneResult(C.Structure):
-    _fields_ = [("N", C.c_uint32), ("n_variants", C.c_uint32), ("elems", C.c_uint32 * 8), ("ms", C.c_float * 8),
-                ("chosen", C.c_uint32)]
+    _fields_ = [("N", C.c_uint32), ("n_variants", C.c_uint32), ("elems", C.c_uint32 * 16), ("ms", C.c_float * 16),
+                ("chosen", C.c_uint32), ("prns_per_cta", C.c_uint32), ("bins_per_cta", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 
 class PlanInfo(C.Structure):
     _fields_ = [("N", C.c_uint32), ("n_prn", C.c_uint32), ("n_dopp", C.c_uint32), ("n_sets", C.c_uint32),
-                ("excl", C.c_uint32), ("block_len", C.c_uint32)]
+                ("excl", C.c_uint32), ("block_len", C.c_uint32), ("xcorr_variant", C.c_uint32)]
 
 
 CANDIDATE_DTYPE = np.dtype([("prn", "u1"), ("reserved", "u1", (7,)), ("f_hz", "<f8"), ("tau_chips", "<f8")])
@@ -246,8 +247,15 @@ class Plan:
         thread for this plan's FFT size on the current device."""
         r = TuneResult()
         check(load().gnss_autotune(self._h, force_elems, C.byref(r)), "gnss_autotune")
-        return {"N": r.N, "chosen": r.chosen,
+        return {"N": r.N, "chosen": r.chosen, "prns_per_cta": r.prns_per_cta, "bins_per_cta": r.bins_per_cta,
                 "timed": {int(r.elems[k]): float(r.ms[k]) for k in range(r.n_variants)}}
+
+    def xcorr_variant(self) -> int:
+        """Correlate-kernel variant code used for this plan's N on the current
+        device now (gnss_plan_get_info)."""
+        info = PlanInfo()
+        check(load().gnss_plan_get_info(self._h, C.byref(info)), "gnss_plan_get_info")
+        return int(info.xcorr_variant)
 
     def surface_shape(self):
         return (self.n_sets, self.n_prn, self.n_dopp, self.N)

@@ -14,6 +14,7 @@ import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -52,15 +53,27 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    objs = []
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    cmds, objs = [], []
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmds.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
+        objs.append(obj)
+
+    def compile_one(cmd):
+        # the translation units are independent: compile them side by side
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+        return cmd, r
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(compile_one, cmds))
+    for cmd, r in results:
         if verbose:
             print(" ".join(cmd), flush=True)
-        subprocess.check_call(cmd)
-        objs.append(obj)
+        if r.stdout and (verbose or r.returncode):
+            print(r.stdout, end="", flush=True)
+        if r.returncode:
+            raise subprocess.CalledProcessError(r.returncode, cmd, r.stdout)
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-lpthread"]
     if verbose:

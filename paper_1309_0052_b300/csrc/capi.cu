@@ -355,6 +355,7 @@ gnss_status gnss_plan_get_info(const gnss_plan* plan, gnss_plan_info* out) {
   out->n_sets = (uint32_t)plan->sets;
   out->excl = (uint32_t)plan->excl;
   out->block_len = plan->desc.coh_ms * (uint32_t)plan->N;
+  out->xcorr_variant = (uint32_t)xcorr_variant(plan->N);
   return GNSS_OK;
 }
 
@@ -505,7 +506,7 @@ static gnss_status plan_batch(const gnss_request* reqs, size_t n_req, size_t scr
         const AcqShape& sh = shape[i];
         nf += (uint64_t)sh.G * sh.B * cpb;
         nc += (uint64_t)(sh.C ? sh.C : sh.D) * sh.B;
-        nx += (uint64_t)sh.P * sh.D;
+        nx += (uint64_t)xcorr_ctas(xcorr_variant(w.N), sh.P, sh.D);
       }
       if (nf > INT32_MAX || nc > INT32_MAX || nx > INT32_MAX)
         return fail(GNSS_EINVAL, "a wave needs more than 2^31 CTAs; lower scratch_budget");
@@ -529,6 +530,7 @@ static void fill_wave(const Wave& w, const gnss_request* reqs, const std::vector
   uint32_t* xb = cb + (n + 1);
   char* cur = scratch;
   const uint32_t cpb = fold_ctas_per_block(w.N);
+  const int variant = xcorr_variant(w.N);
   for (int k = 0; k < n; ++k) {
     const size_t i = w.idx[k];
     const gnss_request& r = reqs[i];
@@ -543,7 +545,7 @@ static void fill_wave(const Wave& w, const gnss_request* reqs, const std::vector
     hr[k].xc = xcorr_args(sh, Y, r.plan->d_cspec, r.plan->d_prns, r.surface_dev, rows, cnt, r.out_dev);
     fb[k + 1] = fb[k] + (uint32_t)(sh.G * sh.B * cpb);
     cb[k + 1] = cb[k] + (uint32_t)((sh.C ? sh.C : sh.D) * sh.B);  // carrier tiles
-    xb[k + 1] = xb[k] + (uint32_t)(sh.P * sh.D);
+    xb[k + 1] = xb[k] + xcorr_ctas(variant, sh.P, sh.D);
     cur += L.total;
   }
   BatchReq* d_reqs = reinterpret_cast<BatchReq*>(desc);
@@ -552,6 +554,7 @@ static void fill_wave(const Wave& w, const gnss_request* reqs, const std::vector
   g.format = w.format;
   g.sets = w.sets;
   g.n = n;
+  g.variant = variant;
   g.reqs = d_reqs;
   g.fold_base = d_base;
   g.car_base = d_base + (n + 1);

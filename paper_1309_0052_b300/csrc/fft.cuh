@@ -654,3 +654,99 @@ __device__ __forceinline__ void fft_class_local(float2 (&v)[16], int t, float2* 
 }
 
 }  // namespace gnss
+
+namespace gnss {
+
+// ---------------------------------------------------------------------------
+// Two independent transforms per thread, interleaved.  Each pass runs the
+// butterflies of both before either exchanges, and each exchange issues both
+// transforms' stores (then loads) together, so the scheduler can overlap one
+// transform's shared-memory latency and barrier with the other's arithmetic.
+// Each transform's own operations are exactly those of the one-transform
+// code, in the same order, so the results are bit-identical to it.
+// ---------------------------------------------------------------------------
+template <int N, bool INV, int NS>
+__device__ __forceinline__ void class_local_rest2(float2 (&va)[16], float2 (&vb)[16], int jp, float2* bufa,
+                                                  const float2* ga, float2* bufb, const float2* gb,
+                                                  const FftTw<N, 16, INV, NS>& tw) {
+  constexpr int T = N / 16;
+  constexpr int R = PassRadix<N, NS, 16>::value;
+  constexpr int Q = 16 / R;
+  pass_compute_tw<N, 16, R, NS, INV>(va, tw);
+  pass_compute_tw<N, 16, R, NS, INV>(vb, tw);
+  if constexpr (N == 8192 && NS * R == N / 2) {
+    lane_pair_radix2<INV>(va, jp, tw.next);
+    lane_pair_radix2<INV>(vb, jp, tw.next);
+  } else if constexpr (NS * R < N) {
+    __syncwarp();  // the class's lanes have read every slot of the class
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const unsigned J = (unsigned)(jp + T * q);
+      const int off = pad_cl((int)((J / NS) * NS * R + (J & (NS - 1))));
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        bufa[off + cl_off(t * NS)] = va[q + Q * t];
+        bufb[off + cl_off(t * NS)] = vb[q + Q * t];
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      va[r] = ga[cl_off(T * r)];
+      vb[r] = gb[cl_off(T * r)];
+    }
+    class_local_rest2<N, INV, NS * R>(va, vb, jp, bufa, ga, bufb, gb, tw.next);
+  }
+}
+
+// Two class-local transforms (see fft_class_local) on buffers bufa, bufb.
+// The caller guarantees that no thread still reads either buffer from an
+// earlier transform (one CTA barrier before the first-pass stores below
+// does that when the same two buffers serve every block).
+template <int N, bool INV>
+__device__ __forceinline__ void fft_class_local2(float2 (&va)[16], float2 (&vb)[16], int t, float2* bufa,
+                                                 float2* bufb, const FftTw<N, 16, INV>& tw) {
+  pass_compute_tw<N, 16, 16, 1, INV>(va, tw);
+  pass_compute_tw<N, 16, 16, 1, INV>(vb, tw);
+  __syncthreads();  // every thread has finished reading both buffers
+  {
+    float2* a = bufa + pad_cl(16 * t);
+    float2* b = bufb + pad_cl(16 * t);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      a[u] = va[u];
+      b[u] = vb[u];
+    }
+  }
+  __syncthreads();
+  const int jp = ClassLocal<N>::perm(t);
+  const float2* ga = bufa + pad_cl(jp);
+  const float2* gb = bufb + pad_cl(jp);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    va[r] = ga[cl_off((N / 16) * r)];
+    vb[r] = gb[cl_off((N / 16) * r)];
+  }
+  class_local_rest2<N, INV, 16>(va, vb, jp, bufa, ga, bufb, gb, tw.next);
+}
+
+// Two Stockham transforms with cached twiddles (see fft_block_tw), on their
+// own buffers; a CTA barrier guards each buffer's reuse.
+template <int N, int E, bool INV, int NS = 1>
+__device__ __forceinline__ void fft_block_tw2(float2 (&va)[E], float2 (&vb)[E], int j, float2* bufa, float2* bufb,
+                                              const FftTw<N, E, INV, NS>& tw) {
+  constexpr int R = PassRadix<N, NS, E>::value;
+  pass_compute_tw<N, E, R, NS, INV>(va, tw);
+  pass_compute_tw<N, E, R, NS, INV>(vb, tw);
+  if constexpr (NS * R < N) {
+    __syncthreads();  // both buffers are free
+    pass_store<N, E, R, NS>(va, j, bufa);
+    pass_store<N, E, R, NS>(vb, j, bufb);
+    __syncthreads();
+    gather_regs<N, E>(va, j, bufa);
+    gather_regs<N, E>(vb, j, bufb);
+    fft_block_tw2<N, E, INV, NS * R>(va, vb, j, bufa, bufb, tw.next);
+  }
+}
+
+}  // namespace gnss

@@ -98,6 +98,7 @@ struct BatchReq {
 // of request r in each kernel are [base[r], base[r + 1]).
 struct BatchGroup {
   int N, format, sets, n;
+  int variant;                // correlate variant the CTA offsets were counted for
   const BatchReq* reqs;       // device [n]
   const uint32_t* fold_base;  // device [n + 1]
   const uint32_t* car_base;   // device [n + 1]
@@ -148,6 +149,17 @@ int xcorr_default_e(int N);
 bool xcorr_valid_e(int N, int code);
 cudaError_t take_stage_timeouts(unsigned* count, cudaStream_t stream);
 void set_xcorr_variant(int N, int E);
+// Correlate CTAs of one request (P PRNs, D bins) under variant 'code': one
+// per (PRN, bin), or per group of PRNs and bins (GNSS_TUNE_TMEM shapes).
+uint32_t xcorr_ctas(int code, int P, int D);
+
+// The TMEM correlate variant (xcorr_tm.cu): variant codes
+// E | GNSS_TUNE_TMEM | GNSS_TUNE_PRNS(K) | GNSS_TUNE_BINS(M).
+bool xcorr_tm_valid(int N, int code);
+int xcorr_tm_prns(int code);
+int xcorr_tm_bins(int code);
+cudaError_t launch_xcorr_tm(int code, const AcqShape& s, const XcorrArgs& a, cudaStream_t stream);
+cudaError_t launch_xcorr_tm_batch(int code, const BatchGroup& g, cudaStream_t stream);
 
 // Fine acquisition (refine.cu).
 struct RefineJob {

@@ -1,13 +1,15 @@
 // tune.cu -- autotuner of the correlate kernel's launch shape.
 //
 // The correlate kernel (conj-multiply, IFFT, |.|^2, non-coherent sum) can
-// hold E = 16 or E = 32 FFT elements per thread: N / E threads per FFT,
+// hold E = 8, 16 or 32 FFT elements per thread: N / E threads per FFT,
 // different register budgets, occupancy and exchange costs; with E = 16 it
-// can also stage the next block by a bulk TMA copy (more shared memory).  Which one is
-// faster depends on the FFT size (and the GPU), so gnss_autotune times every
-// valid choice on a probe shaped like the plan and records the fastest for
-// that FFT size on the current device; every later launch (single or
-// batched) uses it.
+// can also stage the next block by a bulk TMA copy (more shared memory) or
+// run the class-local pass schedule, and the TMEM form keeps the code
+// spectra and sums in tensor memory with a CTA shape of 1-2 PRNs and 1-2
+// Doppler bins.  Which one is faster depends on the FFT size (and the GPU),
+// so gnss_autotune times every valid choice on a probe shaped like the plan
+// and records the fastest for that FFT size on the current device; every
+// later launch (single or batched) uses it.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -26,15 +28,34 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
   gnss_tune_result res;
   memset(&res, 0, sizeof(res));
   res.N = (uint32_t)N;
-  const int cand[6] = {16, 32, 16 | (int)GNSS_TUNE_STAGED, 8, 16 | (int)GNSS_TUNE_CLASS_LOCAL,
-                       32 | (int)GNSS_TUNE_CLASS_LOCAL};
+  const int TM = (int)GNSS_TUNE_TMEM;
+  const int cand[] = {16,
+                      32,
+                      16 | (int)GNSS_TUNE_STAGED,
+                      8,
+                      16 | (int)GNSS_TUNE_CLASS_LOCAL,
+                      32 | (int)GNSS_TUNE_CLASS_LOCAL,
+                      16 | TM,
+                      16 | TM | (int)GNSS_TUNE_PRNS(2),
+                      16 | TM | (int)GNSS_TUNE_BINS(2),
+                      16 | TM | (int)GNSS_TUNE_PRNS(2) | (int)GNSS_TUNE_BINS(2),
+                      16 | TM | (int)GNSS_TUNE_OCC,
+                      32 | TM,
+                      32 | TM | (int)GNSS_TUNE_BINS(2)};
+  constexpr int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
+  static_assert(n_cand <= 16, "gnss_tune_result holds 16 variants");
   if (force_elems) {
-    if (!xcorr_valid_e(N, (int)force_elems))
+    if (force_elems > 0xffffu || !xcorr_valid_e(N, (int)force_elems))
       return fail_status(GNSS_EINVAL, "variant must be 8 (N <= 8192), 16 (N <= 16384), 32 (N >= 1024), 16 | GNSS_TUNE_STAGED "
-                                      "(N <= 8192), 16 | GNSS_TUNE_CLASS_LOCAL (N = 4096 or 8192) or "
-                                      "32 | GNSS_TUNE_CLASS_LOCAL (N = 16384)");
+                                      "(N <= 8192), 16 | GNSS_TUNE_CLASS_LOCAL (N = 4096 or 8192), "
+                                      "32 | GNSS_TUNE_CLASS_LOCAL (N = 16384), or 16 | GNSS_TUNE_TMEM (N = 2048, "
+                                      "4096, 8192; GNSS_TUNE_PRNS 1-2, GNSS_TUNE_BINS 1-2; or GNSS_TUNE_OCC alone at "
+                                      "2048 and 4096) or 32 | GNSS_TUNE_TMEM (N = 16384; GNSS_TUNE_BINS 1-2) where "
+                                      "its tensor-memory columns fit");
     set_xcorr_variant(N, (int)force_elems);
     res.chosen = force_elems;
+    res.prns_per_cta = (uint32_t)xcorr_tm_prns((int)force_elems);
+    res.bins_per_cta = (uint32_t)xcorr_tm_bins((int)force_elems);
     if (out) *out = res;
     return GNSS_OK;
   }
@@ -69,7 +90,7 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
   const int prev = xcorr_variant(N);
   float best = 0.f;
   int best_e = prev;
-  for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < n_cand && e == cudaSuccess; ++k) {
     const int E = cand[k];
     if (!xcorr_valid_e(N, E)) continue;
     set_xcorr_variant(N, E);
@@ -100,6 +121,8 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
   }
   set_xcorr_variant(N, e == cudaSuccess ? best_e : prev);
   res.chosen = (uint32_t)xcorr_variant(N);
+  res.prns_per_cta = (uint32_t)xcorr_tm_prns((int)res.chosen);
+  res.bins_per_cta = (uint32_t)xcorr_tm_bins((int)res.chosen);
   cudaFreeAsync(ws, cs);
   cudaStreamSynchronize(cs);
   if (e0) cudaEventDestroy(e0);

@@ -33,6 +33,52 @@ def _recording(N, coh, B, fmt, seed):
 
 STAGED = 0x100
 CLASS_LOCAL = 0x200
+TMEM = 0x400
+OCC = 0x800
+
+
+def PRNS(k):
+    return (k - 1) << 12
+
+
+def BINS(m):
+    return (m - 1) << 14
+
+
+def _tm_codes(N):
+    """Every TMEM shape the library is built with at N (whether the GPU can
+    take it depends on its occupancy: see _tm_accepted)."""
+    e = {2048: 16, 4096: 16, 8192: 16, 16384: 32}.get(N)
+    if e is None:
+        return []
+    ks = (1, 2) if e == 16 else (1,)
+    occ = [16 | TMEM | OCC] if N in (2048, 4096) else []
+    return [e | TMEM | PRNS(k) | BINS(m) for k in ks for m in (1, 2)] + occ
+
+
+def _tm_accepted(g, plan):
+    """The TMEM shapes the library accepts for the plan's N on this GPU; the
+    one-PRN, one-bin shape must be among them."""
+    ok = []
+    for code in _tm_codes(plan.N):
+        try:
+            assert plan.autotune(code)["chosen"] == code
+            ok.append(code)
+        except g.GnssError as e:
+            assert e.status == g.EINVAL
+    if plan.N in (2048, 4096, 8192, 16384):
+        assert (16 if plan.N < 16384 else 32) | TMEM in ok
+    return ok
+
+
+def _default(N):
+    """The library's default variant at N (the tensor-memory forms at 4096
+    and 16384, which every B300 can hold)."""
+    if N == 4096:
+        return 16 | TMEM | OCC
+    if N == 16384:
+        return 32 | TMEM | BINS(2)
+    return (16 | CLASS_LOCAL) if N == 8192 else 16
 
 
 def _valid(N):
@@ -61,9 +107,10 @@ def test_every_shape_matches_oracle(g, N, half, B):
     x = oracle.unpack(raw, n, fmt)
     S = oracle.surfaces(x, N * 1000, coh, B, half, prns, dopp[0] + dopp[1] * np.arange(dopp[2]), 8)
     ref = oracle.detect(S, prns)
-    default = 32 if N >= 16384 else (16 | CLASS_LOCAL) if N in (4096, 8192) else 16
+    default = _default(N)
     try:
-        for elems in _valid(N):
+        valid = _valid(N) + _tm_accepted(g, plan)
+        for elems in valid:
             assert plan.autotune(elems)["chosen"] == elems
             surf = torch.zeros(plan.surface_shape(), dtype=torch.float32, device="cuda")
             det = plan.acquire(torch.from_numpy(np.ascontiguousarray(raw)).cuda(), n, surface=surf)
@@ -71,7 +118,10 @@ def test_every_shape_matches_oracle(g, N, half, B):
             compare_surfaces(surf.cpu().numpy(), S)
             assert compare_detections(det, ref, S) == 0
         r = plan.autotune()
-        assert r["chosen"] in r["timed"] and sorted(r["timed"]) == sorted(_valid(N))
+        assert r["chosen"] in r["timed"] and sorted(r["timed"]) == sorted(valid)
+        assert (r["prns_per_cta"], r["bins_per_cta"]) == (
+            ((r["chosen"] >> 12) & 3) + 1 if r["chosen"] & TMEM else 1,
+            ((r["chosen"] >> 14) & 3) + 1 if r["chosen"] & TMEM else 1)
         assert all(ms > 0 for ms in r["timed"].values())
     finally:
         plan.autotune(default)
@@ -92,6 +142,18 @@ def test_invalid_shape_rejected(g):
     with pytest.raises(g.GnssError) as e:
         g.Plan(8_192_000, 1, 0, 1, 1, prns=[1]).autotune(32 | CLASS_LOCAL)  # the split is for N = 16384
     assert e.value.status == g.EINVAL
+    for N, code in ((1024, 16 | TMEM),              # not built below 2048
+                    (4096, 32 | TMEM),              # 16 per thread below 16384
+                    (16384, 32 | TMEM | PRNS(2)),   # one PRN per CTA at 16384
+                    (4096, 16 | TMEM | PRNS(3)),    # 1 or 2 PRNs per CTA
+                    (4096, 16 | TMEM | BINS(4)),    # 1 or 2 bins per CTA
+                    (8192, 16 | TMEM | OCC),        # three CTAs per SM: 2048 and 4096 only
+                    (4096, 16 | TMEM | OCC | PRNS(2)),  # one PRN and bin per CTA
+                    (4096, 16 | OCC),               # a form of the TMEM variant
+                    (4096, 16 | TMEM | 0x10000)):   # unknown bits
+        with pytest.raises(g.GnssError) as e:
+            g.Plan(N * 1000, 1, 0, 1, 1, prns=[1]).autotune(code)
+        assert e.value.status == g.EINVAL, (N, hex(code))
 
 
 def test_staged_full_size_and_batch(g):
@@ -122,7 +184,7 @@ def test_staged_full_size_and_batch(g):
             items.append((p, rr, r.n_samples, out, sf))
         g.acquire_batch(items)
         torch.cuda.synchronize()
-        plan.autotune(16 | CLASS_LOCAL)  # the default at N = 4096
+        plan.autotune(16 | CLASS_LOCAL)  # the register form's class-local schedule
         for p, rr, n, out, sf in items:
             o2 = torch.zeros_like(out)
             s2 = torch.zeros_like(sf)
@@ -136,7 +198,7 @@ def test_staged_full_size_and_batch(g):
             A, Bs = sf.cpu().numpy(), s2.cpu().numpy()
             assert np.abs(A - Bs).max() <= 1e-6 * np.abs(Bs).max()
     finally:
-        plan.autotune(16 | CLASS_LOCAL)
+        plan.autotune(_default(4096))
 
 
 def _weak_100ms(g):
@@ -151,7 +213,7 @@ def _fs_8192(g):
 
 @pytest.mark.parametrize("make", [_weak_100ms, _fs_8192])
 def test_class_local_matches_two_barrier_schedule(g, make):
-    """The class-local schedule (the default at N = 4096 and 8192) runs the
+    """The class-local schedule (the register form's at N = 4096 and 8192) runs the
     same butterflies with the same operands as the two-barrier schedule, only
     on other threads -- at 8192 the last radix-2 pass across lane pairs by
     shuffle -- so both give identical surfaces and records: the full 100 ms
@@ -166,7 +228,7 @@ def test_class_local_matches_two_barrier_schedule(g, make):
             det = plan.acquire(raw, n, surface=surf)
             res[code] = (det, surf.cpu().numpy())
     finally:
-        plan.autotune(16 | CLASS_LOCAL)
+        plan.autotune(_default(plan.N))
     (d0, s0), (d1, s1) = res[16], res[16 | CLASS_LOCAL]
     np.testing.assert_array_equal(s0, s1)
     for f in ("prn", "detected", "set", "dopp_bin", "code_phase", "peak", "second", "ratio"):
@@ -224,4 +286,100 @@ def test_split_cluster_batch_equals_alone_and_whole_surface(g):
             np.testing.assert_array_equal(a[f], b[f])
         np.testing.assert_allclose(a["second"], b["second"], rtol=1e-5)
     finally:
-        g.Plan(16_384_000, 1, 0, 1, 1, prns=[1]).autotune(32)  # the default at 16384
+        g.Plan(16_384_000, 1, 0, 1, 1, prns=[1]).autotune(_default(16384))
+
+
+def _case_weak_100ms(g):
+    rec = siggen.weak_100ms()
+    return [(g.Plan.for_recording(rec), rec.raw, rec.n_samples)]
+
+
+def _case_8192_odd(g):
+    # 3 PRNs and 41 bins: the last CTA of a two-PRN or two-bin shape holds one
+    raw, n = _recording(8192, 2, 10, siggen.FMT_2BIT_IQ, 8192)
+    return [(g.Plan(8_192_000, 2, -10000, 500, 41, prns=[3, 9, 30], half_bit=True, fmt=siggen.FMT_2BIT_IQ), raw, n)]
+
+
+def _case_2048_whole(g):
+    # 5 PRNs, 9 bins, 1 ms x 7 blocks; the second variant scans the whole surface
+    raw, n = _recording(2048, 1, 7, siggen.FMT_2BIT_IQ, 2048)
+    return [(g.Plan(2_048_000, 1, -3000, 250, 9, prns=[1, 3, 9, 17, 30], half_bit=hb, fmt=siggen.FMT_2BIT_IQ,
+                    second_whole=sw), raw, n) for hb, sw in ((False, False), (True, True))]
+
+
+def _case_16384(g):
+    raw, n = _recording(16384, 1, 3, siggen.FMT_2BIT_IQ, 16384)
+    return [(g.Plan(16_384_000, 1, -3000, 250, 9, prns=[3, 9, 30], half_bit=True, fmt=siggen.FMT_2BIT_IQ), raw, n)]
+
+
+@pytest.mark.parametrize("make", [_case_weak_100ms, _case_8192_odd, _case_2048_whole, _case_16384])
+def test_tmem_matches_register_form(g, make):
+    """The TMEM variant (code spectra and sums in tensor memory, the next
+    block's spectrum prefetched) runs each block's products, transform and
+    sums operation for operation as the register form: every shape the GPU
+    accepts (1-2 PRNs and 1-2 bins per CTA) gives the default variant's
+    surfaces and records bit for bit -- the full 100 ms workload, odd PRN and
+    bin counts that leave a CTA one PRN or bin short, half-bit sets and the
+    whole-surface second peak."""
+    for plan, raw_np, n in make(g):
+        raw = torch.from_numpy(np.ascontiguousarray(raw_np)).cuda()
+        default = _default(plan.N)
+        try:
+            plan.autotune(default)
+            surf = torch.zeros(plan.surface_shape(), dtype=torch.float32, device="cuda")
+            d0 = plan.acquire(raw, n, surface=surf)
+            s0 = surf.cpu().numpy()
+            for code in _tm_accepted(g, plan):
+                plan.autotune(code)
+                surf = torch.full(plan.surface_shape(), -1.0, dtype=torch.float32, device="cuda")
+                d1 = plan.acquire(raw, n, surface=surf)
+                np.testing.assert_array_equal(surf.cpu().numpy(), s0, err_msg=hex(code))
+                for f in ("prn", "detected", "set", "dopp_bin", "code_phase", "peak", "second", "ratio"):
+                    np.testing.assert_array_equal(d1[f], d0[f], err_msg=hex(code))
+        finally:
+            plan.autotune(default)
+
+
+def test_tmem_batch_equals_alone(g):
+    """A batch of uneven requests (2.048, 4.096 and 8.192 MHz, 20-60 ms) under
+    the two-PRN, two-bin TMEM shape: each request's records and surfaces equal
+    its single launch under the same shape and under the default variant, bit
+    for bit (the batch counts its CTA offsets per request by the shape)."""
+    recs = siggen.batch_requests(8, ms_range=(20, 60))
+    sizes = sorted({r.fs // 1000 for r in recs})
+    probe = {N: g.Plan(N * 1000, 1, 0, 1, 1, prns=[1]) for N in sizes}
+    try:
+        res = {}
+        for which in ("tm", "default"):
+            for N, p in probe.items():
+                if which == "default":
+                    p.autotune(_default(N))
+                else:
+                    acc = _tm_accepted(g, p)
+                    p.autotune(max(acc, key=lambda c: (c >> 12) & 15))  # the most PRNs and bins accepted
+            items = []
+            for r in recs:
+                p = g.Plan.for_recording(r)
+                rr = torch.from_numpy(np.ascontiguousarray(r.raw)).cuda()
+                out = torch.zeros(p.n_prn * 28, dtype=torch.uint8, device="cuda")
+                sf = torch.zeros(p.surface_shape(), dtype=torch.float32, device="cuda")
+                items.append((p, rr, r.n_samples, out, sf))
+            g.acquire_batch(items)
+            torch.cuda.synchronize()
+            batch = [(o.cpu().numpy(), sf.cpu().numpy()) for _, _, _, o, sf in items]
+            alone = []
+            for p, rr, n, out, sf in items:
+                o2, s2 = torch.zeros_like(out), torch.zeros_like(sf)
+                p.acquire_device(rr, n, o2, surface=s2)
+                torch.cuda.synchronize()
+                alone.append((o2.cpu().numpy(), s2.cpu().numpy()))
+            for (oa, sa), (ob, sb) in zip(batch, alone):
+                np.testing.assert_array_equal(oa, ob)
+                np.testing.assert_array_equal(sa, sb)
+            res[which] = alone
+        for (oa, sa), (ob, sb) in zip(res["tm"], res["default"]):
+            np.testing.assert_array_equal(oa, ob)
+            np.testing.assert_array_equal(sa, sb)
+    finally:
+        for N, p in probe.items():
+            p.autotune(_default(N))
