@@ -115,12 +115,16 @@ typedef struct {
  *  dopp_bin   index d of the peak, dopp_hz its frequency
  *  code_phase peak code phase in samples [0, N) (replica delay; with
  *             GNSS_CODE_DOPPLER the delay of block 0)
- *  peak, second, ratio: surface values (sample units squared) and their ratio */
+ *  peak, second, ratio: surface values (sample units squared) and their ratio
+ *  flags      GNSS_DET_* bits of the call that produced the record */
+#define GNSS_DET_STAGE_TIMEOUT 0x01u /* a bounded wait of the staged correlate variant gave up in this call: its
+                                        CTA read the spectra from global memory instead and the results are
+                                        complete, but a copy may have outlived its CTA (see gnss_autotune) */
 typedef struct {
   uint8_t prn;
   uint8_t detected;
   uint8_t set;
-  uint8_t reserved;
+  uint8_t flags;
   int32_t dopp_bin;
   int32_t dopp_hz;
   uint32_t code_phase;
@@ -195,8 +199,11 @@ GNSS_API size_t gnss_recording_bytes(uint32_t format, size_t n_samples);
  *                     the call returns)
  * Errors: GNSS_EINVAL (n_samples < L, misaligned device pointer, NULL
  * arguments), GNSS_ENOMEM, GNSS_ECUDA; with a NULL stream also
- * GNSS_ETIMEOUT when a bounded wait inside the staged correlate kernel gave
- * up since the last such check (the records are then not valid). */
+ * GNSS_ETIMEOUT when a bounded wait of the staged correlate variant gave up
+ * during this call (the records are complete and carry
+ * GNSS_DET_STAGE_TIMEOUT; every entry point reports such a wait through the
+ * flags of its records, and the server fails the request's ticket with
+ * GNSS_ETIMEOUT, keeping its records). */
 GNSS_API gnss_status gnss_acquire(gnss_plan* plan, const void* samples, size_t n_samples, int samples_on_device,
                          gnss_detection* out, float* surface_dev, void* stream);
 
@@ -304,7 +311,9 @@ GNSS_API gnss_status gnss_acquire_zoom(gnss_plan* plan, const void* samples_dev,
  *    a message giving the bytes it needs; nothing is launched.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    device's primary context: like plans, it does not survive
+ *    cudaDeviceReset, after which this entry point must not be called.
  *  - All calls on a device share the one array and it keeps the last call's
  *    contents (every value a call reads is written by that call first).
  *    Calls whose work overlaps on the GPU (other streams, or other threads)
@@ -529,11 +538,6 @@ GNSS_API gnss_status gnss_cancel(gnss_server* srv, uint64_t ticket);
 /* Counters of the server. */
 GNSS_API gnss_status gnss_server_get_stats(gnss_server* srv, gnss_server_stats* out);
 
-/* Testing hook: make the k-th next device allocation of the dispatcher fail
- * (k = 0: the next one; negative: never), as if the device were out of
- * memory; the requests of that batch end with GNSS_ENOMEM and the server
- * carries on.  Nothing is faulted on the device. */
-GNSS_API gnss_status gnss_server_inject_alloc_failure(gnss_server* srv, int k);
 
 /* Launch-shape autotuner of the correlate kernel (the FFT-heavy stage).  It
  * can hold 8, 16 or 32 FFT elements per thread (N/8, N/16 or N/32 threads
@@ -593,12 +597,6 @@ typedef struct {
 
 GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_elems, gnss_tune_result* out);
 
-/* FP32 FMA throughput probe (a measurement aid with no counterpart in the
- * paper; it states the ALU roof the acquisition kernels are held against):
- * 'iters' rounds of 128 dependent-chain FMAs per thread, 4 CTAs of 512
- * threads per SM.  Writes TFLOP/s (2 flops per FMA) and the kernel time in
- * ms (ms may be NULL).  Synchronous. */
-GNSS_API gnss_status gnss_probe_ffma(int iters, double* tflops, double* ms, void* stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 GNSS_API const char* gnss_last_error(void);

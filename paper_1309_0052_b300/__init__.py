@@ -76,7 +76,7 @@ class TrackConfig(C.Structure):
                 ("pll_bw_hz", C.c_float), ("dll_bw_hz", C.c_float), ("reserved", C.c_uint32)]
 
 
-DETECTION_DTYPE = np.dtype([("prn", "u1"), ("detected", "u1"), ("set", "u1"), ("reserved", "u1"),
+DETECTION_DTYPE = np.dtype([("prn", "u1"), ("detected", "u1"), ("set", "u1"), ("flags", "u1"),
                             ("dopp_bin", "<i4"), ("dopp_hz", "<i4"), ("code_phase", "<u4"),
                             ("peak", "<f4"), ("second", "<f4"), ("ratio", "<f4")])
 assert DETECTION_DTYPE.itemsize == 28
@@ -116,6 +116,7 @@ _SIGS = {
     "gnss_server_inject_alloc_failure": ([_P, C.c_int], _st),
     "gnss_autotune": ([_P, C.c_uint32, _P], _st),
     "gnss_probe_ffma": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], _st),
+    "gnss_testing_set_stage_wait_limit": ([C.c_uint32, _P], _st),
     "gnss_last_error": ([], C.c_char_p),
 }
 _lib = None
@@ -282,6 +283,12 @@ class Plan:
         """gnss_acquire_device: out_dev is a CUDA uint8 tensor of n_prn * 28 bytes."""
         check(load().gnss_acquire_device(self._h, _ptr(samples_dev), n_samples, _ptr(out_dev), _ptr(surface),
                                       _stream_ptr(stream)), "gnss_acquire_device")
+
+    def acquire_noalloc(self, samples_dev, n_samples: int, out_dev, surface=None, stream=None) -> None:
+        """gnss_acquire_noalloc: acquire_device with the library's fixed scratch
+        (no allocation).  Asynchronous."""
+        check(load().gnss_acquire_noalloc(self._h, _ptr(samples_dev), n_samples, _ptr(out_dev), _ptr(surface),
+                                          _stream_ptr(stream)), "gnss_acquire_noalloc")
 
     def acquire_device_traced(self, samples_dev, n_samples: int, out_dev, events, surface=None,
                               stream=None) -> None:
@@ -478,6 +485,17 @@ def probe_ffma(iters: int = 4096, stream=None):
     tf, ms = C.c_double(), C.c_double()
     check(load().gnss_probe_ffma(iters, C.byref(tf), C.byref(ms), _stream_ptr(stream)), "gnss_probe_ffma")
     return tf.value, ms.value
+
+
+def set_stage_wait_limit(iters: int, stream=None) -> None:
+    """gnss_testing_set_stage_wait_limit (a testing hook): polls of each
+    staged-correlate wait before it gives up (0: every wait gives up at once;
+    the default is 4194304)."""
+    check(load().gnss_testing_set_stage_wait_limit(iters, _stream_ptr(stream)), "gnss_testing_set_stage_wait_limit")
+
+
+STAGE_TIMEOUT = 0x01  # GNSS_DET_STAGE_TIMEOUT: a record's flags bit
+STAGE_WAIT_DEFAULT = 1 << 22
 
 
 def detections_from_bytes(buf) -> np.ndarray:

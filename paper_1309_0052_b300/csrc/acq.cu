@@ -236,7 +236,7 @@ __device__ __forceinline__ void fold_tile(const FoldArgs& a, int tile) {
   const int m0 = E * ((tile % CPB) * T + threadIdx.x);
   const int g = gb / B, b = gb % B;
   if (a.counters != nullptr && tile == 0)
-    for (int p = threadIdx.x; p < a.P; p += T) a.counters[p] = 0u;
+    for (int p = threadIdx.x; p <= a.P; p += T) a.counters[p] = 0u;  // and the status word
   float ar[E], ai[E];
   fold_samples<N, E, FMT>(a.samples, (int64_t)b * a.coh * N + m0, a.coh, a.gkey[g], ar, ai);
   float4* out = reinterpret_cast<float4*>(a.Z + ((size_t)gb * N + m0));
@@ -349,11 +349,16 @@ __global__ void __launch_bounds__(Cfg<N>::T) k_carrier_fft_batch(const BatchReq*
 // one thread issues a bulk copy (cp.async.bulk) of the N-point row into a
 // shared-memory stage, completing on an mbarrier, while the CTA transforms
 // the current block; the CTA waits on the barrier's phase before it reads
-// the stage.  Every wait is bounded: one that gives up is counted in
-// g_stage_timeouts (read back by the synchronous entry point) and the
-// kernel runs on to its end.
+// the stage.  Every wait is bounded.  The CTA agrees on each wait's outcome;
+// once one has given up it issues no further copy, reads the rest of its
+// spectra from global memory (the results stay complete), sets the call's
+// status word (the records' GNSS_DET_STAGE_TIMEOUT flag) and, before it
+// leaves, waits once more, with the full bound, for the one copy in flight.
 // ---------------------------------------------------------------------------
-__device__ unsigned g_stage_timeouts;
+// try_wait polls of one wait before it gives up (lowered only by the testing
+// entry point, which makes every wait give up at once)
+__device__ unsigned g_stage_wait_limit = 1u << 22;
+constexpr unsigned kStageDrainLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -375,8 +380,8 @@ __device__ __forceinline__ void stage_issue(float2* stg, const float2* src, uint
                : "memory");
 }
 
-__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
+__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -424,15 +429,25 @@ __device__ __forceinline__ void corr_block(const float2* __restrict__ y, int ksh
   asm volatile("" : "+l"(cp));
   float2 v[E];
   if constexpr (ST) {
-    if (!stage_wait(next.mbar, parity)) stage_ok = false;
-    parity ^= 1u;
+    // this block's copy: waited for while the copies are in step; the CTA
+    // agrees on the outcome, so every thread reads the same source and the
+    // issuing thread stops with the others
+    bool landed = false;
+    if (stage_ok) {
+      landed = __syncthreads_and(stage_wait(next.mbar, parity, g_stage_wait_limit)) != 0;
+      if (landed) parity ^= 1u;  // else the copy in flight still owes phase 'parity'
+      else stage_ok = false;
+    }
+    const float2* src = landed ? next.stg : y;  // the stage, or the row itself from L2
     // ksh < 16 <= T (spectrum classes are cut so): only the last element can wrap
-    const float2* ys = next.stg + js;
+    const float2* ys = src + js;
 #pragma unroll
     for (int r = 0; r < E - 1; ++r) v[r] = c_mulconj(ys[T * r], __ldg(cp + j + T * r));
     const int last = js + T * (E - 1);
-    v[E - 1] = c_mulconj(next.stg[last >= N ? last - N : last], __ldg(cp + j + T * (E - 1)));
-    fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw, next);
+    v[E - 1] = c_mulconj(src[last >= N ? last - N : last], __ldg(cp + j + T * (E - 1)));
+    StageIssue issue = next;
+    if (!stage_ok) issue.src = nullptr;  // no copy after a wait gave up
+    fft_block_tw<N, E, true, DB>(v, j, buf0, buf1, phase, tw, issue);
   } else {
     // Y streams from L2 (not kept in L1); the code spectrum goes through the
     // non-coherent path (measured: it too is served from L2, and loads that
@@ -480,7 +495,6 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   __shared__ uint32_t s_idx[32];
   __shared__ unsigned s_last;
   __shared__ __align__(8) uint64_t s_mbar;
-  __shared__ int s_stage_fail;
   const int j = threadIdx.x;
   // thread j ends each transform holding |R|^2 of phases PhaseMap::at(jo, r)
   const int jo = CL ? ClassLocal<(CL ? N : 4096)>::perm(j) : j;
@@ -500,10 +514,7 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
   else if constexpr (TWC) tw.init(jo);
   griddep_wait();  // the spectra and the cleared counters are complete and visible
   if constexpr (ST) {
-    if (j == 0) {
-      s_stage_fail = 0;
-      stage_init(&s_mbar);
-    }
+    if (j == 0) stage_init(&s_mbar);
     __syncthreads();
     if (j == 0) stage_issue(next.stg, yd, next.bytes, &s_mbar);  // block 0 of set 0
   }
@@ -544,13 +555,14 @@ __device__ __forceinline__ void xcorr_tile(const XcorrArgs& a, int tile, float2*
     row_stats<N, E, CL>(acc, jo, a.excl, s_val, s_idx, a.rows + ((size_t)set * a.P + p) * a.D + d);
   }
   if constexpr (ST) {
-    // A wait that gave up may leave a copy in flight: wait for it once more
-    // (bounded) before the CTA's shared memory is released.
-    if (!stage_ok) s_stage_fail = 1;
-    __syncthreads();
-    if (j == 0 && s_stage_fail) {
-      atomicAdd(&g_stage_timeouts, 1u);
-      stage_wait(&s_mbar, parity ^ 1u);
+    // stage_ok is uniform.  After a wait that gave up, one copy may still be
+    // in flight (the one that owes phase 'parity'; none was issued after it):
+    // report the call and wait for that copy with the full bound before the
+    // CTA's shared memory is released.  The status word is ordered before
+    // this CTA's count below by thread 0's fence.
+    if (!stage_ok && j == 0) {
+      atomicOr(a.counters + a.P, (unsigned)GNSS_DET_STAGE_TIMEOUT);
+      stage_wait(&s_mbar, parity, kStageDrainLimit);
     }
   }
   // The last CTA of PRN p (of its D Doppler rows) runs the detection.  The
@@ -1114,15 +1126,10 @@ static cudaError_t batch_n(const BatchGroup& g, cudaStream_t stream) {
   return xcorr_batch_ne<N, 16, false>(g, stream);
 }
 
-// Bounded waits of the staged correlate kernels that gave up since the last
-// call (the counter is reset).
-cudaError_t take_stage_timeouts(unsigned* count, cudaStream_t stream) {
-  unsigned zero = 0;
-  cudaError_t e = cudaMemcpyFromSymbolAsync(count, g_stage_timeouts, sizeof(unsigned), 0, cudaMemcpyDeviceToHost,
-                                            stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  if (e == cudaSuccess && *count)
-    e = cudaMemcpyToSymbolAsync(g_stage_timeouts, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, stream);
+// Polls of each staged-correlate wait before it gives up (testing).
+cudaError_t set_stage_wait_limit(unsigned iters, cudaStream_t stream) {
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_stage_wait_limit, &iters, sizeof(unsigned), 0, cudaMemcpyHostToDevice,
+                                          stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   return e;
 }
@@ -1150,7 +1157,7 @@ AcqScratch scratch_layout(const AcqShape& s) {
   L.y = L.z + al((size_t)s.G * s.B * s.N * sizeof(float2));
   L.rows = L.y + al((size_t)(s.C ? s.C : s.D) * s.B * s.N * sizeof(float2));
   L.counters = L.rows + al((size_t)s.sets * s.P * s.D * sizeof(RowStat));
-  L.total = L.counters + al((size_t)s.P * sizeof(unsigned));
+  L.total = L.counters + al((size_t)(s.P + 1) * sizeof(unsigned));
   return L;
 }
 

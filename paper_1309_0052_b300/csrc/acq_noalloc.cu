@@ -30,7 +30,9 @@ namespace {
 // Device address of g_noalloc_scratch per device.  In host code the array's
 // name is only a host-side stand-in, so the address is looked up once per
 // device with that device current (cudaGetSymbolAddress) and passed to the
-// kernels.
+// kernels.  The cache lives as long as the device's primary context: like
+// the plans, it does not survive cudaDeviceReset (or another teardown of
+// that context), after which the process must not call this entry point.
 std::mutex g_mu;
 void* g_addr[128];
 
@@ -76,10 +78,8 @@ extern "C" GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void
     set_error("gnss_acquire_noalloc: device samples must be 16-byte aligned");
     return GNSS_EINVAL;
   }
-  const size_t L = (size_t)plan->desc.coh_ms * plan->N;
-  size_t B = n_samples / L;
-  if (plan->desc.noncoh && B > plan->desc.noncoh) B = plan->desc.noncoh;
-  if (B < 1 || B > (size_t)INT32_MAX) {
+  const int B = blocks_of(plan, n_samples);
+  if (B < 1) {
     set_error("gnss_acquire_noalloc: n_samples is shorter than one coherent block");
     return GNSS_EINVAL;
   }
@@ -87,23 +87,8 @@ extern "C" GNSS_API gnss_status gnss_acquire_noalloc(gnss_plan* plan, const void
     set_error("gnss_acquire_noalloc: GNSS_SECOND_WHOLE needs a surface buffer");
     return GNSS_EINVAL;
   }
-  AcqShape s;
-  s.fs = (int)plan->desc.fs_hz;
-  s.N = plan->N;
-  s.coh = (int)plan->desc.coh_ms;
-  s.B = (int)B;
-  s.D = plan->D;
-  s.G = plan->G;
-  s.P = plan->P;
-  s.sets = plan->sets;
-  s.excl = plan->excl;
-  s.dopp_min = plan->desc.dopp_min_hz;
-  s.dopp_step = (int)plan->desc.dopp_step_hz;
-  s.format = (int)plan->desc.format;
-  s.second_whole = (plan->desc.flags & GNSS_SECOND_WHOLE) ? 1 : 0;
-  s.code_dopp = (plan->desc.flags & GNSS_CODE_DOPPLER) ? 1 : 0;
-  s.threshold = plan->desc.threshold;
-  spectrum_args(plan, &s);
+  // the same shape as gnss_acquire_device builds, so the same launches
+  const AcqShape s = shape_of(plan, B);
   const AcqScratch lay = scratch_layout(s);
   if (lay.total > GNSS_NOALLOC_SCRATCH_BYTES) {
     set_error("gnss_acquire_noalloc: this request needs " + std::to_string(lay.total) +

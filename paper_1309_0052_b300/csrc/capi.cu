@@ -84,7 +84,7 @@ gnss_status check_plan_device(const gnss_plan* plan) {
   return GNSS_OK;
 }
 
-static AcqShape shape_of(const gnss_plan* plan, int B) {
+AcqShape shape_of(const gnss_plan* plan, int B) {
   AcqShape s;
   s.fs = (int)plan->desc.fs_hz;
   s.N = plan->N;
@@ -105,7 +105,7 @@ static AcqShape shape_of(const gnss_plan* plan, int B) {
   return s;
 }
 
-static int blocks_of(const gnss_plan* plan, size_t n_samples) {
+int blocks_of(const gnss_plan* plan, size_t n_samples) {
   const size_t L = (size_t)plan->desc.coh_ms * plan->N;
   size_t B = n_samples / L;
   if (plan->desc.noncoh && B > plan->desc.noncoh) B = plan->desc.noncoh;
@@ -169,10 +169,10 @@ static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_s
   if (stream == nullptr && out_host) {
     e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    unsigned timeouts = 0;
-    e = take_stage_timeouts(&timeouts, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "stage timeouts");
-    if (timeouts) return fail(GNSS_ETIMEOUT, "a bounded wait of the staged correlate kernel gave up; results invalid");
+    for (int p = 0; p < s.P; ++p)
+      if (out_host[p].flags & GNSS_DET_STAGE_TIMEOUT)
+        return fail(GNSS_ETIMEOUT, "a bounded wait of the staged correlate kernel gave up (records complete, "
+                                   "flagged GNSS_DET_STAGE_TIMEOUT)");
   }
   return GNSS_OK;
 }
@@ -435,7 +435,7 @@ gnss_status gnss_stage_correlate(gnss_plan* plan, const float* spectra_dev, uint
   if (st != GNSS_OK) return st;
   RowStat* rows = reinterpret_cast<RowStat*>(ws);
   unsigned* cnt = reinterpret_cast<unsigned*>(ws + (lay.counters - lay.rows));
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * s.P, cs);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * (s.P + 1), cs);
   if (e == cudaSuccess)
     e = launch_xcorr(s, (const float2*)spectra_dev, plan->d_cspec, plan->d_prns, surface_dev, rows, cnt, out_dev, cs);
   cudaError_t ef = cudaFreeAsync(ws, cs);
@@ -697,6 +697,12 @@ gnss_status gnss_batch_graph_destroy(gnss_batch_graph* g) {
   cudaFree(g->scratch);
   cudaFree(g->desc);
   delete g;
+  return GNSS_OK;
+}
+
+gnss_status gnss_testing_set_stage_wait_limit(uint32_t iters, void* stream) {
+  const cudaError_t e = set_stage_wait_limit(iters, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gnss_testing_set_stage_wait_limit");
   return GNSS_OK;
 }
 

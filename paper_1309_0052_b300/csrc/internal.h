@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "gnss.h"
+#include "gnss_testing.h"
 
 namespace gnss {
 
@@ -59,7 +59,8 @@ struct XcorrArgs {
   int B, D, P, excl;
   float* surface;         // NULL or [sets][P][D][N]
   RowStat* rows;          // [sets][P][D]
-  unsigned* counters;     // [P] zero on entry: CTAs finished per PRN
+  unsigned* counters;     // [P + 1] zero on entry: CTAs finished per PRN, then this
+                          // call's status word (GNSS_DET_* bits for the records)
   const int* prns;        // [P]
   gnss_detection* out;    // [P]
   int dopp_min, dopp_step;
@@ -72,7 +73,7 @@ struct FoldArgs {
   const uint8_t* samples;  // recording
   const int* gkey;         // [G] f mod 1000 per fold group
   float2* Z;               // [G][B][N] folded blocks
-  unsigned* counters;      // NULL or [P] per-PRN counters to clear
+  unsigned* counters;      // NULL or [P + 1] per-PRN counters and status word to clear
   int coh, B, P;
 };
 
@@ -118,7 +119,7 @@ struct AcqScratch {
   size_t z;         // float2 [G][B][N]  folded blocks
   size_t y;         // float2 [D][B][N]  spectra
   size_t rows;      // RowStat [sets][P][D]
-  size_t counters;  // unsigned [P]
+  size_t counters;  // unsigned [P + 1]: per-PRN CTA counters, then the call's status word
   size_t total;
 };
 AcqScratch scratch_layout(const AcqShape& s);
@@ -147,7 +148,8 @@ bool supported_fft_size(int N);
 int xcorr_variant(int N);
 int xcorr_default_e(int N);
 bool xcorr_valid_e(int N, int code);
-cudaError_t take_stage_timeouts(unsigned* count, cudaStream_t stream);
+// Iterations a staged-correlate wait polls before it gives up (testing).
+cudaError_t set_stage_wait_limit(unsigned iters, cudaStream_t stream);
 void set_xcorr_variant(int N, int E);
 // Correlate CTAs of one request (P PRNs, D bins) under variant 'code': one
 // per (PRN, bin), or per group of PRNs and bins (GNSS_TUNE_TMEM shapes).
@@ -195,6 +197,11 @@ struct gnss_plan;
 namespace gnss {
 // Set the spectrum-class fields of a shape from its plan.
 void spectrum_args(const gnss_plan* plan, AcqShape* s);
+// Whole blocks of a recording under a plan (capped by noncoh and INT32_MAX),
+// and the kernels' view of one acquisition of B blocks (capi.cu; every entry
+// point that launches an acquisition builds its shape with these).
+int blocks_of(const gnss_plan* plan, size_t n_samples);
+AcqShape shape_of(const gnss_plan* plan, int B);
 
 // Last-error message (thread-local), set by the C-ABI layer.
 void set_error(const std::string& msg);

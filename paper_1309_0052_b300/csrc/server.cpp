@@ -193,7 +193,10 @@ void CUDART_CB on_batch_done(void* arg) {
         r.result.assign(b->host_out + b->out_off[k], b->host_out + b->out_off[k] + b->n_prn[k]);
         r.state = St::Done;
         r.status = GNSS_OK;
-        srv->stats.completed++;
+        for (const gnss_detection& d : r.result)
+          if (d.flags & GNSS_DET_STAGE_TIMEOUT) r.status = GNSS_ETIMEOUT;  // records kept, call reported
+        if (r.status == GNSS_OK) srv->stats.completed++;
+        else srv->stats.failed++;
       }
       r.t_done = now;
     }

@@ -96,7 +96,7 @@ extern "C" GNSS_API gnss_status gnss_autotune(gnss_plan* plan, uint32_t force_el
     set_xcorr_variant(N, E);
     std::vector<float> t;
     for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
-      e = cudaMemsetAsync(ws + lay.counters, 0, sizeof(unsigned) * s.P, cs);
+      e = cudaMemsetAsync(ws + lay.counters, 0, sizeof(unsigned) * (s.P + 1), cs);
       if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
       if (e == cudaSuccess)
         e = launch_xcorr(s, reinterpret_cast<const float2*>(ws + lay.y), plan->d_cspec, plan->d_prns, nullptr,

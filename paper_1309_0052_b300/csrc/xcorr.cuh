@@ -265,7 +265,7 @@ __device__ __forceinline__ void finalize_prn(const XcorrArgs& a, int p, int sets
       best_ratio = ratio;
       rec.prn = (uint8_t)a.prns[p];
       rec.set = (uint8_t)s;
-      rec.reserved = 0;
+      rec.flags = (uint8_t)__ldcg(a.counters + a.P);  // this call's status word
       rec.dopp_bin = (int32_t)db;
       rec.dopp_hz = a.dopp_min + (int32_t)db * a.dopp_step;
       rec.code_phase = tau;

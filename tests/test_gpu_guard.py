@@ -118,3 +118,25 @@ def test_zoom_refine_and_track_stay_inside_their_buffers(g):
     plan.track(raw, rec.n_samples, cdev, len(cands), trk.bytes, n_int)
     torch.cuda.synchronize()
     assert trk.intact()
+
+
+def test_noalloc_stays_inside_its_buffers(g):
+    """The allocation-free entry point on the 100 ms request and then on the
+    4 ms one (the shared fixed scratch keeps the larger call's contents): its
+    records and surfaces stay inside the caller's buffers, and equal the
+    pool-scratch entry point's."""
+    for make in (siggen.weak_100ms, siggen.plain_4ms):
+        rec = make()
+        plan = g.Plan.for_recording(rec)
+        raw = _dev(rec.raw)
+        shape = plan.surface_shape()
+        out, surf = Guarded(plan.n_prn * 28), Guarded(int(np.prod(shape)) * 4)
+        plan.acquire_noalloc(raw, rec.n_samples, out.bytes, surface=surf.floats(shape))
+        torch.cuda.synchronize()
+        assert out.intact() and surf.intact()
+        out2 = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+        surf2 = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        plan.acquire_device(raw, rec.n_samples, out2, surface=surf2)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.bytes.cpu().numpy(), out2.cpu().numpy())
+        np.testing.assert_array_equal(surf.floats(shape).cpu().numpy(), surf2.cpu().numpy())

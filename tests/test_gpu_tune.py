@@ -383,3 +383,52 @@ def test_tmem_batch_equals_alone(g):
     finally:
         for N, p in probe.items():
             p.autotune(_default(N))
+
+
+def test_staged_wait_gives_up_safely(g):
+    """The staged variant's bounded waits, made to give up at once by the
+    testing hook (every wait polls zero times; the final drain keeps its full
+    bound): each CTA stops issuing copies, reads its spectra from global
+    memory, drains the one copy in flight and flags its call.  The
+    synchronous call returns GNSS_ETIMEOUT, the device-resident and batched
+    calls flag every record with GNSS_DET_STAGE_TIMEOUT, and the records and
+    surfaces themselves are those of a run whose waits all succeed, bit for
+    bit.  With the limit back, the next call carries no flag."""
+    raw_np, n = _recording(4096, 1, 5, siggen.FMT_2BIT_IQ, 4096)
+    plan = g.Plan(4_096_000, 1, -3000, 250, 9, prns=[3, 9, 30], half_bit=True, fmt=siggen.FMT_2BIT_IQ)
+    raw = torch.from_numpy(np.ascontiguousarray(raw_np)).cuda()
+    try:
+        plan.autotune(16 | STAGED)
+        surf = torch.zeros(plan.surface_shape(), dtype=torch.float32, device="cuda")
+        ref = plan.acquire(raw, n, surface=surf)
+        ref_s = surf.cpu().numpy()
+        assert not (ref["flags"] & g.STAGE_TIMEOUT).any()
+        g.set_stage_wait_limit(0)
+        try:
+            out = np.zeros(plan.n_prn, g.DETECTION_DTYPE)
+            with pytest.raises(g.GnssError) as e:
+                plan.acquire(raw, n, out=out)
+            assert e.value.status == g.ETIMEOUT
+            assert (out["flags"] & g.STAGE_TIMEOUT).all()
+            od = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+            s2 = torch.zeros_like(surf)
+            plan.acquire_device(raw, n, od, surface=s2)
+            torch.cuda.synchronize()
+            d2 = g.detections_from_bytes(od.cpu().numpy())
+            assert (d2["flags"] & g.STAGE_TIMEOUT).all()
+            np.testing.assert_array_equal(s2.cpu().numpy(), ref_s)
+            for f in ("prn", "detected", "set", "dopp_bin", "code_phase", "peak", "second", "ratio"):
+                np.testing.assert_array_equal(d2[f], ref[f])
+            ob = torch.zeros_like(od)
+            g.acquire_batch([(plan, raw, n, ob, None)])
+            torch.cuda.synchronize()
+            db = g.detections_from_bytes(ob.cpu().numpy())
+            assert (db["flags"] & g.STAGE_TIMEOUT).all()
+            np.testing.assert_array_equal(db["code_phase"], ref["code_phase"])
+        finally:
+            g.set_stage_wait_limit(g.STAGE_WAIT_DEFAULT)
+        again = plan.acquire(raw, n)
+        assert not (again["flags"] & g.STAGE_TIMEOUT).any()
+        np.testing.assert_array_equal(again["peak"], ref["peak"])
+    finally:
+        plan.autotune(_default(4096))
