@@ -64,7 +64,7 @@ def _L():
         _lib.orc_surfaces.argtypes = [P, P, i64, i64, i, i, i, P, i, P, i, i, i, P]
         _lib.orc_detect.argtypes = [P, i, i, i, i, i, i, d, P, P]
         _lib.orc_refine_eval.argtypes = [P, P, i64, d, P, d, d, P, P]
-        _lib.orc_refine.argtypes = [P, P, i64, d, P, d, d, i, d, P]
+        _lib.orc_refine.argtypes = [P, P, i64, d, P, d, d, i, d, i, P]
         _lib.orc_track.argtypes = [P, P, i64, i64, i, i, P, d, d, d, d, d, P]
         _lib.orc_track.restype = i
     return _lib
@@ -245,14 +245,16 @@ def refine_eval(x, L: int, fs: float, chips, f: float, tau: float):
 
 
 def refine(x, L: int, fs: float, chips, f0: float, tau0: float, max_iter: int = 100,
-           search_hz: float = 0.0) -> dict:
+           search_hz: float = 0.0, flat_accept: bool = True) -> dict:
     """Gradient-ascent fine acquisition from (f0 Hz, tau0 chips), after a
-    Doppler pre-search over +-search_hz at half-lobe spacing fs / (2 L)."""
+    Doppler pre-search over +-search_hz at half-lobe spacing fs / (2 L).
+    flat_accept: also take a Doppler trial that lowers |dP/df| at a loss of
+    at most 1e-5 of P (the FP32 kernel's rule); off, Armijo alone."""
     xr, xi = _split(x)
     chips = np.ascontiguousarray(chips, np.float64)
     r = _Refined()
     _L().orc_refine(_p(xr), _p(xi), int(L), float(fs), _p(chips), float(f0), float(tau0),
-                    int(max_iter), float(search_hz), C.byref(r))
+                    int(max_iter), float(search_hz), int(bool(flat_accept)), C.byref(r))
     return dict(f=r.f, tau=r.tau, P=r.P, iters=r.iters, status=r.status)
 
 

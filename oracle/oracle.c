@@ -558,9 +558,13 @@ typedef struct {
  *   f:   Newton step d_f = g_f / (P (2 pi)^2 T^2 / 6) (closed-form peak
  *        curvature, T = L / fs); trials alpha = 1, 1/2, ... (at most
  *        max_halvings halvings); the first trial is taken when Armijo holds,
- *        P(new) >= P + c1 alpha g_f d_f, or when it reduces |dP/df| without
- *        losing more than 1e-5 of P (near the peak, where the change of P is
- *        below single-precision resolution, the gradient still resolves it);
+ *        P(new) >= P + c1 alpha g_f d_f, or (with flat_accept) when it
+ *        reduces |dP/df| without losing more than 1e-5 of P.  The second
+ *        clause is the rule of the FP32 kernel, where near the peak the
+ *        change of P is below single-precision resolution while the
+ *        gradient still resolves it; in FP64 Armijo alone resolves the peak,
+ *        and the tests show both forms end at the same point (flat_accept is
+ *        on by default so the oracle follows the kernel's rule);
  *   tau: sign step d_tau = s_tau sign(g_tau) (s_tau starts at step0 chip)
  *        with Armijo backtracking, then s_tau <- alpha s_tau.  The slope of
  *        the replica segment is one-sided where samples sit exactly on a
@@ -574,7 +578,7 @@ typedef struct {
  * max_iter iterations (status 2). */
 void orc_refine(const double *xr, const double *xi, int64_t L, double fs,
                 const double *chips, double f0, double tau0, int max_iter,
-                double search_hz, orc_refined *out) {
+                double search_hz, int flat_accept, orc_refined *out) {
   const double c1 = 1e-4, step0 = 0.05, tol_tau = 1e-5, tol_f = 1e-3;
   const int max_halvings = 20;
   double T = (double)L / fs;
@@ -607,7 +611,7 @@ void orc_refine(const double *xr, const double *xi, int64_t L, double fs,
         double Pn, gn[2];
         orc_refine_eval(xr, xi, L, fs, chips, f + alpha * df, tau, &Pn, gn);
         int armijo = Pn >= P + c1 * alpha * g[0] * df;
-        int flatter = fabs(gn[0]) < fabs(g[0]) && Pn >= (1.0 - 1e-5) * P;
+        int flatter = flat_accept && fabs(gn[0]) < fabs(g[0]) && Pn >= (1.0 - 1e-5) * P;
         if (armijo || flatter) {
           f += alpha * df;
           move_f = fabs(alpha * df);

@@ -85,7 +85,8 @@ int main(void) {
   orc_refine_eval(xr, xi, 2 * N, FS, chipd, 1250.5, 100.25, &P, grad);
   orc_refine_eval(xr, xi, 2 * N, FS, chipd, -300.0, -5.75, &P, grad); /* delay outside [0, 1023) */
   orc_refined rf;
-  orc_refine(xr, xi, 2 * N, FS, chipd, 1250.0, 100.0, 12, 500.0, &rf);
+  orc_refine(xr, xi, 2 * N, FS, chipd, 1250.0, 100.0, 12, 500.0, 1, &rf);
+  orc_refine(xr, xi, 2 * N, FS, chipd, 1250.0, 100.0, 12, 500.0, 0, &rf);
 
   /* tracking channel: a 4 ms recording at 2.048 MHz (above the chip rate) */
   const int64_t fs2 = 2048000, n2 = 4 * 2048;

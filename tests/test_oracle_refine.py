@@ -126,3 +126,63 @@ def test_ascent_converges_to_truth_noise_free():
     assert abs(r["tau"] - 300.3) < 1e-3
     P0, _ = oracle.refine_eval(x, L, FS, chips, 1234.5 + 180.0, 300.3 + 0.3)
     assert r["P"] > P0
+
+
+def _refine_12ms_starts():
+    """The 12 ms workload's satellites, started where the plain acquisition
+    would hand them over: the nearest 500 Hz bin and the nearest sample."""
+    rec = siggen.refine_12ms()
+    x = oracle.unpack(rec.raw, rec.n_samples, rec.fmt)
+    starts = []
+    for s in rec.sats:
+        f0 = 500.0 * round(s.dopp_hz / 500.0)
+        tau0 = round(s.code_phase_chips * rec.N / 1023.0) * 1023.0 / rec.N
+        starts.append((s.prn, f0, tau0))
+    return rec, x, starts
+
+
+def test_ascent_endpoint_is_the_local_maximum_noisy():
+    """The ascent's result, not only its rule: for every satellite of the
+    noisy 12 ms workload (coarse start, 250 Hz pre-search, 10 ms window), a
+    brute-force search of P(f, tau) with plain loops around the oracle's
+    endpoint -- a line of +-0.5 Hz at 1e-2 Hz, a line of +-0.01 chip at 1e-4
+    chip, and a +-0.5 Hz x +-0.01 chip grid at 0.05 Hz x 1e-3 chip -- finds no
+    cell above the endpoint's power beyond the ascent's stopping tolerance
+    (tau step < 1e-5 chip: P within 2e-5 of the peak's on the correlation
+    triangle, whose slope is about 2 P per chip)."""
+    rec, x, starts = _refine_12ms_starts()
+    Lw = 10 * rec.N
+    for prn, f0, tau0 in starts:
+        chips = oracle.ca_code(prn).astype(float)
+        r = oracle.refine(x, Lw, rec.fs, chips, f0, tau0, max_iter=100, search_hz=250.0)
+        fs_, ts_, Ps = r["f"], r["tau"], r["P"]
+        best = 0.0
+        for k in range(-50, 51):
+            best = max(best, oracle.refine_eval(x, Lw, rec.fs, chips, fs_ + 0.01 * k, ts_)[0])
+        for k in range(-100, 101):
+            best = max(best, oracle.refine_eval(x, Lw, rec.fs, chips, fs_, ts_ + 1e-4 * k)[0])
+        for a in range(-10, 11):
+            for b in range(-10, 11):
+                best = max(best, oracle.refine_eval(x, Lw, rec.fs, chips, fs_ + 0.05 * a, ts_ + 1e-3 * b)[0])
+        assert best <= Ps * (1.0 + 5e-5), (prn, best / Ps - 1.0)
+        assert Ps > oracle.refine_eval(x, Lw, rec.fs, chips, f0, tau0)[0], prn
+
+
+def test_flat_acceptance_leaves_fp64_endpoints_unchanged():
+    """The Doppler step's second acceptance clause (a trial that lowers
+    |dP/df| while losing at most 1e-5 of P) exists for the FP32 kernel, where
+    changes of P near the peak are below single precision.  In FP64 Armijo
+    alone resolves the peak: with and without the clause the ascent ends at
+    the same point (within its stopping tolerances) for every satellite of
+    the 12 ms workload and for 40 seeded random off-peak starts."""
+    rec, x, starts = _refine_12ms_starts()
+    Lw = 10 * rec.N
+    rprn, rf, rtau = siggen.refine_candidates(rec)
+    cases = starts + list(zip(rprn[:40].tolist(), rf[:40].tolist(), rtau[:40].tolist()))
+    for prn, f0, tau0 in cases:
+        chips = oracle.ca_code(int(prn)).astype(float)
+        a = oracle.refine(x, Lw, rec.fs, chips, f0, tau0, max_iter=100, search_hz=250.0, flat_accept=True)
+        b = oracle.refine(x, Lw, rec.fs, chips, f0, tau0, max_iter=100, search_hz=250.0, flat_accept=False)
+        assert abs(a["f"] - b["f"]) < 5e-3, (prn, f0, tau0, a, b)
+        assert abs(a["tau"] - b["tau"]) < 5e-5, (prn, f0, tau0, a, b)
+        assert abs(a["P"] - b["P"]) <= 1e-6 * max(a["P"], b["P"]), (prn, f0, tau0, a, b)
