@@ -282,7 +282,7 @@ def run_code_doppler(g, torch, rec, stream, flush, steps):
     return res
 
 
-def run_refine(g, torch, rec, stream, steps):
+def run_refine(g, torch, rec, stream, steps, peak_tflops):
     """Fine acquisition of the 12 ms recording: the detections of a plain
     acquisition (true candidates) plus 1000 seeded random candidates, refined
     over 10 ms on the device (Doppler pre-search +-250 Hz, then gradient
@@ -316,6 +316,12 @@ def run_refine(g, torch, rec, stream, steps):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     out = np.frombuffer(out_dev.cpu().numpy().tobytes(), g.REFINED_DTYPE)
+    # algorithmic FP32 work of the ascent actually run: per sample of the
+    # L = coh * N window, 20 flops for P alone (carrier rotation 6, wipe-off
+    # 6, interpolated chip 4, z += w c 4) and 10 more for the gradient sums
+    # ((n - L/2) w c 6, -w slope 4); evaluations counted by the kernel
+    L = coh * plan.N
+    flops = float(L * (20.0 * out["n_eval"].astype(np.float64).sum() + 30.0 * out["n_eval_grad"].astype(np.float64).sum()))
     T = coh * plan.N / rec.fs
     truth = {s.prn: s for s in rec.sats}
     df, dt = [], []
@@ -327,16 +333,21 @@ def run_refine(g, torch, rec, stream, steps):
         mid = s.code_phase_chips - s.dopp_hz * T / (2 * 1540.0)
         dt.append((out[k]["tau_chips"] - mid + 511.5) % 1023 - 511.5)
     t = statistics.median(ms)
+    achieved = flops / (t * 1e-3) / 1e12
     return {"workload": "refine_12ms: 2.048 MHz int8, %d true + %d random candidates, 10 ms window, "
                         "pre-search +-250 Hz, <= 100 iterations" % (len(true), len(rprn)),
             "ms_per_call": t, "candidates_per_s": len(cands) / (t * 1e-3),
             "true_candidates": len(df),
             "rms_doppler_error_hz": float(np.sqrt(np.mean(np.square(df)))) if df else None,
             "rms_delay_error_chips": float(np.sqrt(np.mean(np.square(dt)))) if dt else None,
-            "status_counts": {int(k): int(v) for k, v in zip(*np.unique(out["status"], return_counts=True))}}
+            "status_counts": {int(k): int(v) for k, v in zip(*np.unique(out["status"], return_counts=True))},
+            "evaluations_per_call": {"p": int(out["n_eval"].sum()), "p_and_gradient": int(out["n_eval_grad"].sum())},
+            "roofline": {"bound": "alu", "kernel": "k_refine", "achieved": achieved, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": achieved / peak_tflops, "flops_per_call": flops,
+                         "flop_count": "per window sample: 20 for P alone, 30 with the gradient (of derived peak)"}}
 
 
-def run_track(g, torch, rec, stream, steps, n_chan=1280):
+def run_track(g, torch, rec, stream, steps, peak_tops, n_chan=1280):
     """Tracking channels over the 1 s recording: the 8 injected satellites
     from perturbed truth plus seeded channels on every PRN at random (f, tau)
     up to n_chan, 1000 intervals of 1 ms each, one launch; channel-ms per
@@ -373,7 +384,19 @@ def run_track(g, torch, rec, stream, steps, n_chan=1280):
     recs = recs.reshape(len(rec.sats), n_int)[:, -200:]
     lock = [float(np.mean(r["zp"][:, 1] ** 2) / max(np.mean(r["zp"][:, 0] ** 2), 1e-30)) for r in recs]
     t = statistics.median(ms)
-    return {"workload": "track_1s: 4.096 MHz 2-bit, 1 s, %d channels (8 injected satellites + seeded channels "
+    # algorithmic operations per channel-sample (32): wipe-off x e^{-j theta}
+    # (complex product, 6 flops) and the carrier's advance (rotation, 6),
+    # the 64-bit code NCO advance (2 integer ops), the early / prompt / late
+    # replica chips (index and bit, 2 integer ops each: 6) and their sign-
+    # applied accumulation (3 x (2 sign flips + 2 adds): 12); against the
+    # issue roof of one operation per lane of each SM sub-partition per cycle
+    cs = len(cands) * rec.n_samples
+    ops = 32.0 * cs
+    achieved = ops / (t * 1e-3) / 1e12
+    return {"roofline": {"bound": "issue", "kernel": "k_track", "achieved": achieved, "peak": peak_tops,
+                         "unit": "Tops/s", "frac": achieved / peak_tops, "ops_per_channel_sample": 32,
+                         "peak_basis": "148 SMs x 4 sub-partitions x 32 lanes x max SM clock (of derived)"},
+            "workload": "track_1s: 4.096 MHz 2-bit, 1 s, %d channels (8 injected satellites + seeded channels "
                         "on every PRN), 1000 intervals of 1 ms, E/P/L spacing 1 chip, PLL 15 Hz, DLL 2 Hz" % n_chan,
             "ms_per_launch": t, "channel_ms_per_s": len(cands) * n_int / (t * 1e-3),
             "sample_correlations_per_s": 3 * len(cands) * rec.n_samples / (t * 1e-3),
@@ -397,6 +420,13 @@ def run_zoom(g, torch, rec, stream, steps):
         fine = plan.zoom(raw, rec.n_samples, det, 5, 1, stream=stream)
         ms.append((time.perf_counter() - t0) * 1e3)
     truth = {s.prn: s.dopp_hz + 0.5 * s.dopp_rate * (rec.n_samples / rec.fs) for s in rec.sats}
+    # algorithmic FP32 work of one call: per detection, the fine bins' fold and
+    # forward FFTs and one PRN's correlations over every block (the counts of
+    # the acquisition itself, on 11 bins)
+    D, B, N = 11, plan.n_blocks(rec.n_samples), plan.N
+    flops = float(len(det)) * (_flops_total(1, D, B, N, rec.coh_ms))
+    peak = 148 * 128 * 2 * 2032e6 / 1e12
+    zoom_tflops = flops / (statistics.median(ms) * 1e-3) / 1e12
     ec = [int(d["dopp_hz"]) - truth[int(d["prn"])] for d in det if int(d["prn"]) in truth]
     ez = [int(d["dopp_hz"]) - truth[int(d["prn"])] for d in fine if int(d["prn"]) in truth]
     return {"workload": "weak_100ms detections, fine grid 50 Hz over +-250 Hz (11 bins) per detection",
@@ -404,7 +434,87 @@ def run_zoom(g, torch, rec, stream, steps):
             "rms_doppler_error_hz": {"coarse": float(np.sqrt(np.mean(np.square(ec)))) if ec else None,
                                      "zoom": float(np.sqrt(np.mean(np.square(ez)))) if ez else None},
             "ratio_mean": {"coarse": float(det["ratio"].mean()) if len(det) else None,
-                           "zoom": float(fine["ratio"].mean()) if len(fine) else None}}
+                           "zoom": float(fine["ratio"].mean()) if len(fine) else None},
+            "roofline": {"bound": "alu", "kernel": "zoom call (k_fold, k_carrier_fft, correlate; host time)",
+                         "achieved": zoom_tflops, "peak": peak, "unit": "TFLOP/s", "frac": zoom_tflops / peak,
+                         "flops_per_call": flops,
+                         "note": "host-timed call of a few small launches: launch- and latency-bound, not ALU-bound"}}
+
+
+def _chip_err(a, b):
+    """Circular code-delay difference in chips, in [-511.5, 511.5)."""
+    return (a - b + 511.5) % 1023.0 - 511.5
+
+
+def zoom_vs_refine(g, torch, rec, zoom, stream=None, steps=5):
+    """The two fine searches on the same coarse detections of one recording:
+    gnss_acquire_zoom (grid step / zoom over +-1 step; coherent blocks of the
+    plan, integrated over the whole recording) and gnss_refine (gradient
+    ascent over a 10 ms window from the recording start, pre-search +-half a
+    coarse step).  Errors against the injected truth at the middle of the
+    samples each method integrates; times per call (host clock, stream
+    synchronised, records back on the host)."""
+    plan = g.Plan.for_recording(rec)
+    raw = torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda()
+    det = plan.acquire(raw, rec.n_samples)
+    truth = {s.prn: s for s in rec.sats}
+    det = det[(det["detected"] == 1) & np.isin(det["prn"], list(truth))]
+    cands = g.candidates(det["prn"], det["dopp_hz"].astype(float), det["code_phase"] * 1023.0 / rec.N)
+    win_ms = 10
+    search = rec.dopp_step_hz / 2.0
+
+    def do_zoom():
+        return plan.zoom(raw, rec.n_samples, det, zoom, 1, stream=stream)
+
+    def do_refine():
+        return plan.refine(raw, rec.n_samples, cands, win_ms, 100, search_hz=search, stream=stream)
+
+    fine, ref = do_zoom(), do_refine()
+    tz, tr = [], []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        do_zoom()
+        t1 = time.perf_counter()
+        do_refine()
+        t2 = time.perf_counter()
+        tz.append((t1 - t0) * 1e3)
+        tr.append((t2 - t1) * 1e3)
+    t_all = 0.5 * rec.n_samples / rec.fs  # coarse and zoom: the whole recording
+    t_win = 0.5 * win_ms * 1e-3           # refine: its window
+    rows = []
+    for d, z, r in zip(det, fine, ref):
+        s = truth[int(d["prn"])]
+        f_all, c_all = rec.truth_at(s, t_all)
+        f_win, c_win = rec.truth_at(s, t_win)
+        rows.append({"prn": int(d["prn"]), "cn0_dbhz": s.cn0_dbhz, "bit_edge_in_window": s.bit_edge_ms < win_ms,
+                     "doppler_error_hz": {"coarse": float(d["dopp_hz"] - f_all), "zoom": float(z["dopp_hz"] - f_all),
+                                          "refine": float(r["f_hz"] - f_win)},
+                     "code_error_chips": {"coarse": float(_chip_err(d["code_phase"] * 1023.0 / rec.N, c_all)),
+                                          "zoom": float(_chip_err(z["code_phase"] * 1023.0 / rec.N, c_all)),
+                                          "refine": float(_chip_err(r["tau_chips"], c_win))}})
+
+    def rms(key, method, subset=None):
+        v = [row[key][method] for row in rows if subset is None or subset(row)]
+        return float(np.sqrt(np.mean(np.square(v)))) if v else None
+
+    clean = lambda row: not row["bit_edge_in_window"]
+    return {"detections": len(rows), "zoom": zoom, "zoom_step_hz": rec.dopp_step_hz / zoom,
+            "refine_window_ms": win_ms, "ms_per_call": {"zoom": statistics.median(tz), "refine": statistics.median(tr)},
+            "rms_doppler_error_hz": {m: rms("doppler_error_hz", m) for m in ("coarse", "zoom", "refine")},
+            "rms_code_error_chips": {m: rms("code_error_chips", m) for m in ("coarse", "zoom", "refine")},
+            "rms_doppler_error_hz_edge_free_window": {m: rms("doppler_error_hz", m, clean)
+                                                      for m in ("coarse", "zoom", "refine")},
+            "per_detection": rows}
+
+
+def run_zoom_vs_refine(g, torch, stream):
+    """zoom_vs_refine on the 12 ms recording (2.048 MHz, 1 ms blocks, 500 Hz
+    grid, no bit edge in the first 10 ms) and on the 100 ms one (4.096 MHz,
+    10 ms blocks with half-bit sets, 250 Hz grid)."""
+    import siggen
+    return {"refine_12ms": zoom_vs_refine(g, torch, siggen.refine_12ms(), 10, stream),
+            "weak_100ms": zoom_vs_refine(g, torch, siggen.weak_100ms(), 10, stream)}
 
 
 def run_fft_sizes(g, torch, stream, flush, steps, peak_tflops, sizes=(2048, 4096, 8192, 16384)):
@@ -704,12 +814,13 @@ def run_ours(args):
         line["code_doppler"] = run_code_doppler(g, torch, long_rec, stream, flush, steps=10)
     if not args.no_zoom:
         line["zoom"] = run_zoom(g, torch, rec, stream, steps=10)
+        line["zoom_vs_refine"] = run_zoom_vs_refine(g, torch, stream)
     if not args.no_sizes:
         line["fft_sizes"] = run_fft_sizes(g, torch, stream, flush, steps=5, peak_tflops=peak_tflops)
     if ref_rec is not None:
-        line["refine"] = run_refine(g, torch, ref_rec, stream, steps=10)
+        line["refine"] = run_refine(g, torch, ref_rec, stream, steps=10, peak_tflops=peak_tflops)
     if trk_rec is not None:
-        line["track"] = run_track(g, torch, trk_rec, stream, steps=3)
+        line["track"] = run_track(g, torch, trk_rec, stream, steps=3, peak_tops=sms * 4 * 32 * clock_for_peak * 1e6 / 1e12)
     if batch:
         line["batch"] = run_batch(g, torch, batch, stream, flush, steps=3, peak_tflops=peak_tflops)
     if serve:

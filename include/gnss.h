@@ -363,7 +363,8 @@ typedef struct {
   float power;         /* P at the refined point                  */
   uint32_t iters;      /* accepted steps                          */
   int32_t status;      /* 0 converged (Newton step < 1e-3 Hz, tau step < 1e-5 chip), 1 stuck, 2 max_iter */
-  uint32_t reserved;
+  uint16_t n_eval;     /* evaluations of P alone (pre-search, tau trials), saturating at 65535 */
+  uint16_t n_eval_grad; /* evaluations of P with its gradient (f trials, after accepted tau steps) */
 } gnss_refined;
 
 /* P and its gradient for n (PRN, f, tau) points, one CTA per point.

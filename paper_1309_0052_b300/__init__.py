@@ -62,7 +62,7 @@ class PlanInfo(C.Structure):
 
 CANDIDATE_DTYPE = np.dtype([("prn", "u1"), ("reserved", "u1", (7,)), ("f_hz", "<f8"), ("tau_chips", "<f8")])
 REFINED_DTYPE = np.dtype([("f_hz", "<f8"), ("tau_chips", "<f8"), ("power", "<f4"), ("iters", "<u4"),
-                          ("status", "<i4"), ("reserved", "<u4")])
+                          ("status", "<i4"), ("n_eval", "<u2"), ("n_eval_grad", "<u2")])
 assert CANDIDATE_DTYPE.itemsize == 24 and REFINED_DTYPE.itemsize == 32
 
 TRACK_DTYPE = np.dtype([("f_hz", "<f8"), ("tau_chips", "<f8"), ("ze", "<f4", (2,)), ("zp", "<f4", (2,)),

@@ -299,21 +299,31 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
   const double Tw = (double)J.L / J.fs;
   const double curv = (2.0 * 3.14159265358979323846) * (2.0 * 3.14159265358979323846) * Tw * Tw / 6.0;
   double f = c.f_hz, tau = c.tau_chips, s_tau = 0.05;
+  // evaluations run (P alone, P and gradient): the work of this candidate
+  unsigned n_p = 0, n_pg = 0;
+  auto eval_p = [&](double ff, double tt, float* rd, EvalPoint* p) {
+    ++n_p;
+    return evaluate<T, FMT, false>(J, chips, sp, ff, tt, rd, p);
+  };
+  auto eval_pg = [&](double ff, double tt, float* rd, EvalPoint* p) {
+    ++n_pg;
+    return evaluate<T, FMT, true>(J, chips, sp, ff, tt, rd, p);
+  };
   if (search_hz > 0.0) {
     const double d = J.fs / (2.0 * (double)J.L);
     const int K = (int)floor(search_hz / d);
-    float best = evaluate<T, FMT, false>(J, chips, sp, c.f_hz, tau, red, &pt).P;
+    float best = eval_p(c.f_hz, tau, red, &pt).P;
     for (int k = 1; k <= K; ++k)
       for (int sg = -1; sg <= 1; sg += 2) {
         const double fk = c.f_hz + sg * k * d;
-        const float Pk = evaluate<T, FMT, false>(J, chips, sp, fk, tau, red, &pt).P;
+        const float Pk = eval_p(fk, tau, red, &pt).P;
         if (Pk > best) {
           best = Pk;
           f = fk;
         }
       }
   }
-  EvalOut e = evaluate<T, FMT, true>(J, chips, sp, f, tau, red, &pt);
+  EvalOut e = eval_pg(f, tau, red, &pt);
   int it = 0, status = 2;
   for (; it < max_iter; ++it) {
     double move_f = 0.0, move_t = 0.0;
@@ -321,7 +331,7 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
     if (df != 0.0) {
       double alpha = 1.0;
       for (int h = 0; h <= 20; ++h) {
-        const EvalOut en = evaluate<T, FMT, true>(J, chips, sp, f + alpha * df, tau, red, &pt);
+        const EvalOut en = eval_pg(f + alpha * df, tau, red, &pt);
         const bool armijo = (double)en.P >= (double)e.P + c1 * alpha * (double)e.gf * df;
         const bool flatter = fabsf(en.gf) < fabsf(e.gf) && (double)en.P >= (1.0 - 1e-5) * (double)e.P;
         if (armijo || flatter) {
@@ -340,12 +350,12 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
       double alpha = 1.0;
       bool accepted = false;
       for (int h = 0; h <= 20; ++h) {
-        const EvalOut en = evaluate<T, FMT, false>(J, chips, sp, f, tau + alpha * dt, red, &pt);
+        const EvalOut en = eval_p(f, tau + alpha * dt, red, &pt);
         if ((double)en.P >= (double)e.P + c1 * alpha * (double)e.gt * dt) {
           tau += alpha * dt;
           s_tau *= alpha;
           move_t = fabs(alpha * dt);
-          e = evaluate<T, FMT, true>(J, chips, sp, f, tau, red, &pt);
+          e = eval_pg(f, tau, red, &pt);
           accepted = true;
           break;
         }
@@ -354,12 +364,12 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
       if (!accepted) {  // a segment slope is one-sided at an exact kink: try the other direction
         alpha = 1.0;
         for (int h = 0; h <= 20; ++h) {
-          const EvalOut en = evaluate<T, FMT, false>(J, chips, sp, f, tau - alpha * dt, red, &pt);
+          const EvalOut en = eval_p(f, tau - alpha * dt, red, &pt);
           if (en.P > e.P) {
             tau -= alpha * dt;
             s_tau *= alpha;
             move_t = fabs(alpha * dt);
-            e = evaluate<T, FMT, true>(J, chips, sp, f, tau, red, &pt);
+            e = eval_pg(f, tau, red, &pt);
             accepted = true;
             break;
           }
@@ -385,7 +395,8 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
     r.power = e.P;
     r.iters = (uint32_t)it;
     r.status = status;
-    r.reserved = 0;
+    r.n_eval = (uint16_t)min(n_p, 65535u);
+    r.n_eval_grad = (uint16_t)min(n_pg, 65535u);
     out[blockIdx.x] = r;
   }
 }

@@ -97,6 +97,14 @@ class Recording:
         """Injected code phase in samples at t = 0, in [0, N)."""
         return (sat.code_phase_chips * self.N / CHIPS) % self.N
 
+    def truth_at(self, sat: Sat, t: float):
+        """Injected Doppler (Hz) and code delay (chips, in [0, 1023)) of a
+        satellite at time t (s) from the recording start: the Doppler moves
+        at its rate, and the delay falls by the carrier cycles over 1540
+        (code Doppler), as synthesize builds them."""
+        cycles = sat.dopp_hz * t + 0.5 * sat.dopp_rate * t * t
+        return sat.dopp_hz + sat.dopp_rate * t, (sat.code_phase_chips - cycles / L1_PER_CHIP) % CHIPS
+
 
 def draw_sats(rng, n_sats, cn0, dopp, rec_ms, rate=0.0, edge_range=(0.0, 20.0), prns=None):
     """Draw n_sats distinct satellites: PRN, C/N0 ~ U(cn0), Doppler ~ U(dopp),

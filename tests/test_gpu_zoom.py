@@ -80,3 +80,52 @@ def test_zoom_rejects(g, coarse):
         sub.zoom(raw, rec.n_samples, det[:1], 5, 1)  # PRN not in that plan
     assert e.value.status == g.EINVAL
     assert len(plan.zoom(raw, rec.n_samples, det[:0], 5, 1)) == 0
+
+
+def _zvr(g, name):
+    import bench
+    return bench.zoom_vs_refine(g, torch, getattr(siggen, name)(), 10, steps=1)
+
+
+def test_zoom_and_refine_on_the_same_detections(g):
+    """The two fine searches side by side, on each recording's own coarse
+    detections.  Both beat the coarse grid where their integration allows:
+    on the 12 ms recording (1 ms coherent blocks, a clean 10 ms window)
+    refinement, whose 10 ms window resolves Doppler ten times finer than a
+    1 ms block, beats the zoom, which beats the coarse grid; on the 100 ms
+    recording (10 ms blocks with half-bit sets) the zoom beats the coarse
+    grid, and where no navigation-bit edge falls in refinement's 10 ms window
+    the two agree within the zoom's half step -- for the GPU results and for
+    the oracle's zoom (its acquisition on the fine grid) and refinement."""
+    a = _zvr(g, "refine_12ms")
+    e = a["rms_doppler_error_hz"]
+    assert a["detections"] == 8
+    assert e["refine"] < e["zoom"] < e["coarse"], e
+    assert a["rms_code_error_chips"]["refine"] < a["rms_code_error_chips"]["coarse"]
+    b = _zvr(g, "weak_100ms")
+    e = b["rms_doppler_error_hz"]
+    assert b["detections"] >= 3 and e["zoom"] < e["coarse"], e
+    half = b["zoom_step_hz"] / 2
+    clean = [r for r in b["per_detection"] if not r["bit_edge_in_window"]]
+    assert len(clean) >= 2
+    for r in clean:
+        dz, dr = r["doppler_error_hz"]["zoom"], r["doppler_error_hz"]["refine"]
+        assert abs(dz - dr) <= half + 0.1, r  # truths at 50 and 5 ms differ by rate x 45 ms < 0.03 Hz
+    # the oracle's zoom and refinement of the same clean detections
+    rec = siggen.weak_100ms()
+    x = oracle.unpack(rec.raw, rec.n_samples, rec.fmt)
+    plan = g.Plan.for_recording(rec)
+    det = plan.acquire(torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda(), rec.n_samples)
+    edge = {s.prn: s.bit_edge_ms for s in rec.sats}
+    step = rec.dopp_step_hz
+    for d in det[det["detected"] == 1]:
+        prn = int(d["prn"])
+        if edge.get(prn, 0.0) < 10.0:
+            continue
+        fgrid = (int(d["dopp_hz"]) + (step // 10) * np.arange(-10, 11)).astype(np.int64)
+        S = oracle.surfaces(x, rec.fs, rec.coh_ms, rec.n_blocks, True, [prn], fgrid, 8)
+        ref = oracle.detect(S, [prn])[0]
+        fz = float(fgrid[ref["dopp_bin"]])
+        r = oracle.refine(x, 10 * rec.N, rec.fs, oracle.ca_code(prn).astype(float), float(d["dopp_hz"]),
+                          d["code_phase"] * 1023.0 / rec.N, max_iter=100, search_hz=step / 2)
+        assert abs(fz - r["f"]) <= half, (prn, fz, r["f"])
