@@ -184,7 +184,13 @@ def make_workloads(args):
                         by_idx[i] = r
                 batch = [by_idx[i] for i in range(args.batch_requests)]
             if not args.no_serve:
-                serve = siggen.serving_requests(args.serve_pool)
+                chunks = [list(range(i, args.serve_pool, 16)) for i in range(min(16, args.serve_pool))]
+                parts = list(ex.map(siggen.serving_requests_subset, [(args.serve_pool, c) for c in chunks]))
+                by_idx = {}
+                for c, part in zip(chunks, parts):
+                    for i, r in zip(c, part):
+                        by_idx[i] = r
+                serve = [by_idx[i] for i in range(args.serve_pool)]
     return rec, batch, serve, long_rec, ref_rec, trk_rec
 
 
@@ -556,69 +562,83 @@ def run_fft_sizes(g, torch, stream, flush, steps, peak_tflops, sizes=(2048, 4096
             "sizes": res}
 
 
-def run_serving(g, serve, rate, seconds, seed=1309005205):
-    """Poisson arrivals at 'rate' requests/s for 'seconds' through
-    gnss_submit / gnss_poll; latency = submit -> result observed (host clock)."""
+def run_serving_curve(g, serve, rates, seconds, bound_ms, seed=1309005205):
+    """Latency against offered load through gnss_submit / gnss_poll: one
+    server (plans and code spectra made resident once, before timing) takes
+    Poisson arrivals over the pooled recordings at each rate for 'seconds';
+    latency = submit -> result seen by the polling thread (host clock).  With
+    bound_ms the server refuses submissions whose projected wait exceeds it
+    (GNSS_EBUSY, counted as refused), which bounds latency past saturation."""
     import threading
-    srv = g.Server(max_batch=64, streams=2)
+    srv = g.Server(max_batch=64, streams=2, max_queue_wait_ms=bound_ms)
     descs = [g.Server.desc_for(r) for r in serve]
-    for d, r in zip(descs, serve):  # plans and code spectra resident before timing
+    for d, r in zip(descs, serve):
         srv.wait(srv.submit(d, r.raw, r.n_samples), 600000)
-    rng = np.random.default_rng(seed)
     req_cells = [_cells(32, r.n_dopp, r.N, r.n_blocks, r.coh_ms) for r in serve]
-    pending = {}
-    done = []
-    done_cells = [0]
-    busy = 0
-    lock = threading.Lock()
-    stop = threading.Event()
+    rng = np.random.default_rng(seed)
+    points = []
+    for rate in rates:
+        pending, done, done_cells, queued = {}, [], [0], []
+        refused = 0
+        lock = threading.Lock()
+        stop = threading.Event()
 
-    def poller():
-        while not stop.is_set() or pending:
-            with lock:
-                items = list(pending.items())
-            for t, (t0, kk) in items:
-                try:
-                    r = srv.poll(t)
-                except g.GnssError:
-                    r = "err"
-                if r is not None:
-                    with lock:
-                        pending.pop(t, None)
-                    done.append(time.perf_counter() - t0)
-                    done_cells[0] += req_cells[kk % len(serve)]
-            time.sleep(0.0002)
+        def poller():
+            while not stop.is_set() or pending:
+                with lock:
+                    items = list(pending.items())
+                for t, (t0, kk) in items:
+                    try:
+                        r = srv.poll(t)
+                    except g.GnssError:
+                        r = "err"
+                    if r is not None:
+                        with lock:
+                            pending.pop(t, None)
+                        done.append(time.perf_counter() - t0)
+                        done_cells[0] += req_cells[kk % len(serve)]
+                time.sleep(0.0002)
 
-    th = threading.Thread(target=poller, daemon=True)
-    th.start()
-    t_start = time.perf_counter()
-    t_next = t_start
-    k = 0
-    while t_next - t_start < seconds:
-        now = time.perf_counter()
-        if now < t_next:
-            time.sleep(t_next - now)
-        r = serve[k % len(serve)]
-        try:
-            tk = srv.submit(descs[k % len(serve)], r.raw, r.n_samples)
-            with lock:
-                pending[tk] = (time.perf_counter(), k)
-        except g.GnssError:
-            busy += 1
-        k += 1
-        t_next += rng.exponential(1.0 / rate)
-    stop.set()
-    th.join(timeout=600)
-    t_total = time.perf_counter() - t_start
+        def sampler():
+            while not stop.is_set():
+                queued.append(srv.stats()["queued"])
+                time.sleep(0.05)
+
+        th, ts = threading.Thread(target=poller, daemon=True), threading.Thread(target=sampler, daemon=True)
+        refused0 = srv.stats()["refused"]
+        th.start()
+        ts.start()
+        t_start = time.perf_counter()
+        t_next, k = t_start, 0
+        while t_next - t_start < seconds:
+            now = time.perf_counter()
+            if now < t_next:
+                time.sleep(t_next - now)
+            r = serve[k % len(serve)]
+            try:
+                tk = srv.submit(descs[k % len(serve)], r.raw, r.n_samples)
+                with lock:
+                    pending[tk] = (time.perf_counter(), k)
+            except g.GnssError:
+                refused += 1
+            k += 1
+            t_next += rng.exponential(1.0 / rate)
+        stop.set()
+        th.join(timeout=600)
+        ts.join(timeout=10)
+        t_total = time.perf_counter() - t_start
+        lat = np.array(done) * 1e3
+        pct = lambda q: float(np.percentile(lat, q)) if len(lat) else None
+        points.append({"offered_req_per_s": rate, "seconds": seconds, "submitted": k, "refused": refused,
+                       "refused_by_bound": srv.stats()["refused"] - refused0, "completed": len(done),
+                       "requests_per_s": len(done) / t_total, "cells_per_s": done_cells[0] / t_total,
+                       "p50_ms": pct(50), "p99_ms": pct(99), "p999_ms": pct(99.9),
+                       "queued_mean": float(np.mean(queued)) if queued else 0.0,
+                       "queued_max": int(max(queued)) if queued else 0})
     srv.close()
-    lat = np.array(done) * 1e3
-    return {"offered_req_per_s": rate, "seconds": seconds, "submitted": k, "refused_busy": busy,
-            "completed": len(done), "requests_per_s": len(done) / t_total,
-            "cells_per_s": done_cells[0] / t_total,
-            "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
-            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
-            "workload": "Poisson arrivals over %d pooled recordings 10-500 ms, fs up to 16.384 MHz, 2-bit, "
-                        "32 PRN, +-10 kHz at 250/500 Hz" % len(serve)}
+    return {"workload": "Poisson arrivals over %d pooled recordings 10-500 ms, fs up to 16.384 MHz, 2-bit, "
+                        "32 PRN, +-10 kHz at 250/500 Hz" % len(serve),
+            "admission_bound_ms": bound_ms, "device_budget_gib": 16, "points": points}
 
 
 def run_cufft_comparator(g, torch, plan, raw_dev, n_samples, stream, flush, steps, ours_ms):
@@ -824,8 +844,8 @@ def run_ours(args):
     if batch:
         line["batch"] = run_batch(g, torch, batch, stream, flush, steps=3, peak_tflops=peak_tflops)
     if serve:
-        line["serving"] = [run_serving(g, serve, float(r), args.serve_seconds)
-                           for r in args.serve_rates.split(",") if r.strip()]
+        line["serving"] = run_serving_curve(g, serve, [float(r) for r in args.serve_rates.split(",") if r.strip()],
+                                            args.serve_seconds, args.serve_bound_ms)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(rec, args)
     if ws > 1:
@@ -1001,10 +1021,12 @@ def main():
     ap.add_argument("--no-zoom", action="store_true")
     ap.add_argument("--no-sizes", action="store_true", help="skip the correlate at N = 2048 ... 16384")
     ap.add_argument("--batch-requests", type=int, default=256)
-    ap.add_argument("--serve-rates", default="50,100,200",
-                    help="offered Poisson arrival rates (requests/s), one serving run each")
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--serve-pool", type=int, default=8)
+    ap.add_argument("--serve-rates", default="50,100,150,175,200,250",
+                    help="offered request rates of the serving curve (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="seconds of Poisson arrivals per rate")
+    ap.add_argument("--serve-pool", type=int, default=64, help="distinct recordings in the serving pool")
+    ap.add_argument("--serve-bound-ms", type=int, default=250,
+                    help="server admission bound on the projected wait (ms, 0 = none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

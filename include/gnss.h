@@ -491,7 +491,9 @@ typedef struct {
   uint32_t max_batch;         /* requests per batched launch (0 = 64) */
   uint32_t streams;           /* streams carrying batches, two in flight each (0 = 2, at most 16) */
   uint32_t queue_timeout_ms;  /* fail requests still queued after this long with GNSS_ETIMEOUT (0 = never) */
-  uint32_t reserved;
+  uint32_t max_queue_wait_ms; /* admission bound: refuse with GNSS_EBUSY a request whose projected wait
+                                 (the work queued and in flight ahead of it, plus its own, at the server's
+                                 measured throughput) exceeds this (0 = no bound) */
 } gnss_server_config;
 
 typedef struct {
@@ -501,7 +503,7 @@ typedef struct {
   uint64_t batches;               /* batched launches so far */
   uint64_t queued;                /* requests waiting for admission now */
   uint32_t batches_in_flight;
-  uint32_t reserved;
+  uint32_t refused;               /* submissions refused by the admission bound (saturating) */
   size_t device_bytes_reserved;   /* device bytes of batches in flight now */
 } gnss_server_stats;
 
@@ -517,8 +519,12 @@ GNSS_API gnss_status gnss_server_destroy(gnss_server* srv);
 /* Queue one recording (host memory, copied before return: the caller may
  * free it) for acquisition with the plan 'desc' describes; *ticket names it.
  * Thread-safe.  Errors: GNSS_EINVAL (descriptor, length, GNSS_SECOND_WHOLE),
- * GNSS_EBUSY (host staging full, or the request alone exceeds the device
- * budget), GNSS_ECANCELLED (server shutting down). */
+ * GNSS_EBUSY (host staging full, the request alone exceeds the device
+ * budget, or -- with max_queue_wait_ms -- its projected wait exceeds that
+ * bound: the work of the requests queued and in flight plus its own, in
+ * algorithmic FLOPs of the acquisition, over the throughput the server has
+ * achieved while busy; no bound applies before the first batch completes),
+ * GNSS_ECANCELLED (server shutting down). */
 GNSS_API gnss_status gnss_submit(gnss_server* srv, const gnss_plan_desc* desc, const void* host_samples,
                                  size_t n_samples, uint64_t* ticket);
 

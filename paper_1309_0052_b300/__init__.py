@@ -40,13 +40,13 @@ class Request(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("device_mem_budget", C.c_size_t), ("host_staging_bytes", C.c_size_t), ("max_batch", C.c_uint32),
-                ("streams", C.c_uint32), ("queue_timeout_ms", C.c_uint32), ("reserved", C.c_uint32)]
+                ("streams", C.c_uint32), ("queue_timeout_ms", C.c_uint32), ("max_queue_wait_ms", C.c_uint32)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
                 ("batches", C.c_uint64), ("queued", C.c_uint64), ("batches_in_flight", C.c_uint32),
-                ("reserved", C.c_uint32), ("device_bytes_reserved", C.c_size_t)]
+                ("refused", C.c_uint32), ("device_bytes_reserved", C.c_size_t)]
 
 
 class TuneResult(C.Structure):
@@ -413,8 +413,9 @@ class Server:
     """Request server with continuous batching (gnss_server_*)."""
 
     def __init__(self, device_mem_budget: int = 0, host_staging_bytes: int = 0, max_batch: int = 0,
-                 streams: int = 0, queue_timeout_ms: int = 0):
-        cfg = ServerConfig(device_mem_budget, host_staging_bytes, max_batch, streams, queue_timeout_ms, 0)
+                 streams: int = 0, queue_timeout_ms: int = 0, max_queue_wait_ms: int = 0):
+        cfg = ServerConfig(device_mem_budget, host_staging_bytes, max_batch, streams, queue_timeout_ms,
+                           max_queue_wait_ms)
         h = _P()
         check(load().gnss_server_create(C.byref(cfg), C.byref(h)), "gnss_server_create")
         self._h = h

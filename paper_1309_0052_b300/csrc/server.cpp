@@ -17,10 +17,16 @@
 //           one device allocation per batch, H2D copies, batched kernels,
 //           D2H of the records, completion through cudaLaunchHostFunc.
 //   poll / wait: results are handed out once and released.
+//   admission bound (optional): a submission whose projected wait -- the work
+//           queued and in flight ahead of it plus its own, over the
+//           throughput achieved while busy -- exceeds max_queue_wait_ms is
+//           refused with GNSS_EBUSY, so that latency past saturation stays
+//           bounded instead of growing with the queue.
 #include <cuda_runtime.h>
 #include <string.h>
 
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <iterator>
@@ -112,6 +118,7 @@ struct Req {
   std::string error;
   std::vector<gnss_detection> result;
   Clock::time_point t_submit, t_done;
+  double work = 0.0;  // algorithmic FLOPs of the acquisition (admission bound)
 };
 
 struct Batch;
@@ -135,6 +142,12 @@ struct gnss_server {
   uint64_t next_ticket = 1;
   bool stop = false;
   int inject_alloc_fail = -1;  // fail the k-th next device allocation (testing hook)
+  // throughput while busy, for the admission bound: work completed and time
+  // with at least one batch in flight, both weighted toward recent batches
+  // (each completion scales the sums by kRateDecay); busy_mark is the start
+  // of the busy time not yet added
+  double work_in_flight = 0.0, work_done = 0.0, busy_s = 0.0;
+  std::chrono::steady_clock::time_point busy_mark;
   gnss_server_stats stats;
   std::thread dispatcher;
 };
@@ -146,6 +159,7 @@ struct Batch {
   gnss_server* srv;
   std::vector<std::shared_ptr<Req>> reqs;
   size_t bytes = 0;
+  double work = 0.0;  // sum of its requests' work
   void* dev = nullptr;
   gnss_detection* host_out = nullptr;  // pinned records of the whole batch (in the arena)
   std::vector<size_t> out_off;         // record offset per request
@@ -176,6 +190,38 @@ size_t device_need(const gnss_plan* plan, size_t n_samples) {
          scratch_layout(s).total + 1024;
 }
 
+// Algorithmic FLOPs of one acquisition (5 N log2 N per complex FFT, 6 per
+// complex product): per (bin, block) the wipe-off and fold of L samples and a
+// forward FFT, per (PRN, bin, block) the conj-multiply, IFFT, |.|^2 and sum.
+double acquisition_work(const gnss_plan* plan, size_t n_samples) {
+  const size_t L = (size_t)plan->desc.coh_ms * plan->N;
+  size_t B = n_samples / L;
+  if (plan->desc.noncoh && B > plan->desc.noncoh) B = plan->desc.noncoh;
+  const double N = plan->N, lg = std::log2(N);
+  return (double)plan->D * (double)B * (8.0 * (double)L + 5.0 * N * lg) +
+         (double)plan->P * plan->D * (double)B * (5.0 * N * lg + 10.0 * N);
+}
+
+// Weight of the earlier batches in the throughput estimate, per completion
+// (about the last 20 batches count).
+constexpr double kRateDecay = 0.95;
+
+// Achieved throughput (FLOP/s) while at least one batch was in flight,
+// weighted toward recent batches; 0 before the first batch completes.
+// Caller holds srv->mu.
+double busy_rate(const gnss_server* srv, Clock::time_point now) {
+  double t = srv->busy_s;
+  if (srv->in_flight > 0) t += std::chrono::duration<double>(now - srv->busy_mark).count();
+  return (srv->work_done > 0.0 && t > 0.0) ? srv->work_done / t : 0.0;
+}
+
+// A batch completed (caller holds srv->mu, in_flight still counts it).
+void account_completion(gnss_server* srv, double work, Clock::time_point now) {
+  srv->busy_s = kRateDecay * srv->busy_s + std::chrono::duration<double>(now - srv->busy_mark).count();
+  srv->work_done = kRateDecay * srv->work_done + work;
+  srv->busy_mark = now;
+}
+
 void CUDART_CB on_batch_done(void* arg) {
   Batch* b = static_cast<Batch*>(arg);
   gnss_server* srv = b->srv;
@@ -202,6 +248,8 @@ void CUDART_CB on_batch_done(void* arg) {
     }
     srv->arena.release(reinterpret_cast<unsigned char*>(b->host_out));
     srv->reserved -= b->bytes;
+    srv->work_in_flight -= b->work;
+    account_completion(srv, b->work, now);
     srv->in_flight--;
   }
   srv->cv.notify_all();
@@ -309,6 +357,7 @@ void dispatch_loop(gnss_server* srv) {
       const size_t need = device_need(plan, r->n_samples);
       if (srv->reserved + b->bytes + need > srv->cfg.device_mem_budget) break;
       b->bytes += need;
+      b->work += r->work;
       b->reqs.push_back(r);
       plans.push_back(plan);
       srv->queue.pop_front();
@@ -330,7 +379,8 @@ void dispatch_loop(gnss_server* srv) {
     }
     for (auto& r : b->reqs) r->state = St::Running;
     srv->reserved += b->bytes;
-    srv->in_flight++;
+    srv->work_in_flight += b->work;
+    if (srv->in_flight++ == 0) srv->busy_mark = Clock::now();
     srv->stats.batches++;
     b->stream = srv->streams[srv->next_stream++ % srv->streams.size()];
     const bool inject = srv->inject_alloc_fail == 0;
@@ -388,6 +438,8 @@ void dispatch_loop(gnss_server* srv) {
       fail_requests(srv, b->reqs, fs, msg);
       srv->arena.release(reinterpret_cast<unsigned char*>(b->host_out));
       srv->reserved -= b->bytes;
+      srv->work_in_flight -= b->work;
+      account_completion(srv, 0.0, Clock::now());  // its busy time, no work
       srv->in_flight--;
       delete b;
       srv->cv.notify_all();
@@ -465,6 +517,7 @@ gnss_status gnss_server_destroy(gnss_server* srv) {
 gnss_status gnss_submit(gnss_server* srv, const gnss_plan_desc* desc, const void* host_samples, size_t n_samples,
                         uint64_t* ticket) {
   if (!srv || !desc || !host_samples || !ticket) return fail_status(GNSS_EINVAL, "NULL argument");
+  double work = 0.0;
   if (desc->flags & GNSS_SECOND_WHOLE) return fail_status(GNSS_EINVAL, "GNSS_SECOND_WHOLE needs surfaces; not served");
   if (desc->fs_hz == 0 || desc->fs_hz % 1000 || !supported_fft_size((int)(desc->fs_hz / 1000)) || desc->coh_ms < 1 ||
       desc->n_dopp < 1 || desc->n_dopp > 100000 || desc->format > GNSS_FMT_2BIT_IQ || (desc->prn_mask & 0xFFFFFFFFull) == 0 ||
@@ -487,13 +540,31 @@ gnss_status gnss_submit(gnss_server* srv, const gnss_plan_desc* desc, const void
     probe.sets = (desc->flags & GNSS_HALF_BIT) ? 2 : 1;
     if (device_need(&probe, n_samples) > srv->cfg.device_mem_budget)
       return fail_status(GNSS_EBUSY, "request needs more device memory than the server budget");
+    work = acquisition_work(&probe, n_samples);
   }
   auto r = std::make_shared<Req>();
   r->desc = *desc;
   r->n_samples = n_samples;
   r->rec_bytes = rec_bytes_of(desc->format, n_samples);
+  r->work = work;
   std::unique_lock<std::mutex> lk(srv->mu);
   if (srv->stop) return fail_status(GNSS_ECANCELLED, "server is shutting down");
+  if (srv->cfg.max_queue_wait_ms) {
+    // projected wait: the work queued and in flight ahead of this request,
+    // plus its own, at the throughput achieved while busy
+    const double rate = busy_rate(srv, Clock::now());
+    if (rate > 0.0) {
+      double ahead = srv->work_in_flight + work;
+      for (const auto& q : srv->queue) ahead += q->work;
+      const double wait_ms = 1e3 * ahead / rate;
+      if (wait_ms > (double)srv->cfg.max_queue_wait_ms) {
+        if (srv->stats.refused < 0xFFFFFFFFu) srv->stats.refused++;
+        return fail_status(GNSS_EBUSY, "projected wait " + std::to_string((long long)wait_ms) +
+                                           " ms exceeds the admission bound of " +
+                                           std::to_string(srv->cfg.max_queue_wait_ms) + " ms");
+      }
+    }
+  }
   r->staging = srv->arena.alloc(r->rec_bytes);
   if (!r->staging) return fail_status(GNSS_EBUSY, "host staging full: too many queued recordings");
   memcpy(r->staging, host_samples, r->rec_bytes);

@@ -313,3 +313,11 @@ def serving_requests(n_req: int, seed: int = SEED_BASE + 5, ms_range=(10, 500),
     and coherent length 500 / step ms."""
     return batch_requests(n_req, seed=seed, fs_choices=fs_choices, ms_range=ms_range,
                           sats_range=(2, 12), cn0=(28.0, 48.0))
+
+
+def serving_requests_subset(arg) -> list:
+    """Requests idx of serving_requests(n) with its default parameters, for
+    generation in parallel worker processes: arg = (n, idx)."""
+    n, idx = arg
+    params = _batch_params(n, SEED_BASE + 5, (2_048_000, 4_096_000, 8_192_000, 16_384_000), (10, 500), (2, 12))
+    return [_batch_recording(params[i], (28.0, 48.0)) for i in idx]

@@ -163,3 +163,47 @@ def test_injected_allocation_failure(g, recs, alone):
     s = srv.stats()
     assert s["failed"] == 1 and s["device_bytes_reserved"] == 0
     srv.close()
+
+
+def test_admission_bound_refuses_on_the_host(g, recs, alone):
+    """The admission bound (max_queue_wait_ms): once a batch has completed and
+    the server knows its throughput, a submission whose projected wait -- the
+    work queued and in flight ahead of it plus its own, over that throughput
+    -- exceeds the bound is refused at once with GNSS_EBUSY (counted in the
+    stats); every accepted request still completes with its records alone.
+    The decision is made on the host; nothing is faulted on the device."""
+    rec, ref = recs[-1], alone[-1]  # the 100 ms request
+    srv = g.Server(max_batch=4, streams=2, max_queue_wait_ms=20)
+    desc = g.Server.desc_for(rec)
+    try:
+        np.testing.assert_array_equal(srv.wait(srv.submit(desc, rec.raw, rec.n_samples), 60000), ref)
+        tickets, refused = [], 0
+        for _ in range(300):
+            try:
+                tickets.append(srv.submit(desc, rec.raw, rec.n_samples))
+            except g.GnssError as e:
+                assert e.status == g.EBUSY and "admission bound" in str(e)
+                refused += 1
+        assert refused > 0 and len(tickets) > 0
+        for t in tickets:
+            np.testing.assert_array_equal(srv.wait(t, 60000), ref)
+        st = srv.stats()
+        assert st["refused"] == refused
+        assert st["completed"] == len(tickets) + 1 and st["failed"] == 0
+    finally:
+        srv.close()
+
+
+def test_no_admission_bound_by_default(g, recs, alone):
+    """Without a bound a burst queues up in full (only memory and staging
+    limit admission) and nothing is refused."""
+    rec, ref = recs[-1], alone[-1]
+    srv = g.Server(max_batch=4, streams=2)
+    desc = g.Server.desc_for(rec)
+    try:
+        tickets = [srv.submit(desc, rec.raw, rec.n_samples) for _ in range(40)]
+        for t in tickets:
+            np.testing.assert_array_equal(srv.wait(t, 60000), ref)
+        assert srv.stats()["refused"] == 0
+    finally:
+        srv.close()
