@@ -144,6 +144,21 @@ __device__ __forceinline__ void tm_st32(uint32_t ta, const float (&r)[32]) {
                "f"(r[30]), "f"(r[31])
                : "memory");
 }
+// 8 columns (the twiddle bases of one radix-16 pass): load and tied wait.
+__device__ __forceinline__ void tm_ld8(uint32_t ta, float (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]),
+               "=f"(r[6]), "=f"(r[7])
+               : "r"(ta));
+}
+__device__ __forceinline__ void tm_wait_ld8(float (&r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3]), "+f"(r[4]), "+f"(r[5]),
+               "+f"(r[6]), "+f"(r[7])
+               :
+               : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Launch shape of the TMEM variant: E = 16 elements per thread (class-local
 // schedule at 4096 and 8192, cached twiddles otherwise) with the next block
@@ -172,7 +187,11 @@ struct TmShape {
     // two PRNs run their transforms interleaved instead, see fft_class_local2)
     static constexpr bool prefetch = E == 16 && K == 1 && !O;
     static constexpr int per_prn = acc_regs ? 2 * E : 3 * E;
-    static constexpr int stride = (K * per_prn + 31) / 32 * 32;  // columns of one warp slot
+    // the occupancy form at 4096 keeps the two twiddled passes' bases (w, w^2,
+    // w^4, w^8 each: 16 floats) in TMEM too, after the PRNs' columns
+    static constexpr bool tw_tmem = O && CL && N == 4096;
+    static constexpr int tw_cols = tw_tmem ? 16 : 0;
+    static constexpr int stride = (K * per_prn + tw_cols + 31) / 32 * 32;  // columns of one warp slot
     static constexpr int alloc = tm_pow2_cols(SLOTS * stride);
     static_assert(alloc <= 512, "TMEM has 512 columns");
   };
@@ -256,6 +275,70 @@ __device__ __forceinline__ void tm_read_sums(uint32_t ta, float (&acc)[E]) {
   }
 }
 
+// The class-local 4096-point inverse transform (fft_class_local, the same
+// passes and operations) with each twiddled pass's bases read from TMEM
+// columns ta .. ta + 8 (pass NS = 16) and ta + 8 .. ta + 16 (NS = 256) right
+// before the pass: 16 registers fewer live through the transform.
+__device__ __forceinline__ TwBase16 tw_unpack(const float (&w)[8]) {
+  TwBase16 b;
+  b.w1 = make_float2(w[0], w[1]);
+  b.w2 = make_float2(w[2], w[3]);
+  b.w4 = make_float2(w[4], w[5]);
+  b.w8 = make_float2(w[6], w[7]);
+  return b;
+}
+
+__device__ __forceinline__ void tw_to_tmem(const TwBase16& a, const TwBase16& b, uint32_t ta) {
+  const float w[16] = {a.w1.x, a.w1.y, a.w2.x, a.w2.y, a.w4.x, a.w4.y, a.w8.x, a.w8.y,
+                       b.w1.x, b.w1.y, b.w2.x, b.w2.y, b.w4.x, b.w4.y, b.w8.x, b.w8.y};
+  tm_st16(ta, w);
+}
+
+__device__ __forceinline__ void fft4096_cl_tmtw(float2 (&v)[16], int t, float2* buf, uint32_t ta_tw) {
+  constexpr int N = 4096, T = N / 16;
+  {
+    FftTw<N, 16, true, 1> none;  // pass 1 (NS = 1) takes no twiddles
+    pass_compute_tw<N, 16, 16, 1, true>(v, none);
+  }
+  {
+    float2* b = buf + pad_cl(16 * t);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[u] = v[u];
+  }
+  // each pass's bases are requested one exchange ahead, so the TMEM load
+  // completes under the barrier and the gathers
+  float w[8];
+  tm_ld8(ta_tw, w);
+  __syncthreads();
+  const int jp = ClassLocal<N>::perm(t);
+  const float2* g = buf + pad_cl(jp);  // element jp + T r sits at g[cl_off(T r)]
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = g[cl_off(T * r)];
+  {
+    tm_wait_ld8(w);
+    FftTw<N, 16, true, 16> tw;
+    tw.tw[0] = tw_unpack(w);
+    pass_compute_tw<N, 16, 16, 16, true>(v, tw);
+  }
+  tm_ld8(ta_tw + 8u, w);
+  __syncwarp();  // the class's lanes have read every slot of the class
+  {
+    // butterfly jp of the NS = 16 pass writes y[(jp / 16) 256 + (jp mod 16) + 16 u]
+    float2* b = buf + pad_cl((jp / 16) * 256 + (jp & 15));
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[cl_off(16 * u)] = v[u];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = g[cl_off(T * r)];
+  {
+    tm_wait_ld8(w);
+    FftTw<N, 16, true, 256> tw;
+    tw.tw[0] = tw_unpack(w);
+    pass_compute_tw<N, 16, 16, 256, true>(v, tw);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // One CTA: PRNs p0 .. p0 + kk - 1 (kk <= K) of the tile rows u0 .. u0 + mm - 1
 // (mm <= M; a row is a Doppler bin, or the bin bin_order names).  Each bin
@@ -317,6 +400,9 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
       }
     }
   }
+  // with the twiddle bases in TMEM: the two twiddled passes' bases, after the PRNs' columns
+  const uint32_t ttw = tq + (uint32_t)(K * Cl::per_prn);
+  if constexpr (Cl::tw_tmem) tw_to_tmem(tw.next.tw[0], tw.next.next.tw[0], ttw);
   tm_wait_st();  // the first block reads them back
   auto bin_at = [&](int u) { return a.bin_order ? __ldg(a.bin_order + u) : u; };
   // bin d's spectrum: its own row, or its class's row read K bins further
@@ -395,7 +481,7 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
         }
         if constexpr (K == 1) {
           // one PRN: straight-line block
-          if constexpr (X::TWC) tw.launder();
+          if constexpr (X::TWC && !Cl::tw_tmem) tw.launder();
           float2 v[E];
           if constexpr (Cl::prefetch) {
             tm_product<E>(tq, y, v);
@@ -414,7 +500,10 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
               for (int r = 0; r < 16; ++r) s16[r] = 0.f;
             }
           }
-          if constexpr (CL) {
+          if constexpr (Cl::tw_tmem) {
+            fft4096_cl_tmtw(v, j, phase ? buf1 : buf0, ttw);
+            phase ^= 1;
+          } else if constexpr (CL) {
             fft_class_local<N, true>(v, j, phase ? buf1 : buf0, tw);
             phase ^= 1;
           } else if constexpr (X::TWC) {
