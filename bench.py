@@ -562,6 +562,56 @@ def run_fft_sizes(g, torch, stream, flush, steps, peak_tflops, sizes=(2048, 4096
             "sizes": res}
 
 
+def run_variants(g, torch, rec, stream, flush, steps=20):
+    """Every correlate variant the library accepts on this GPU, forced in turn
+    and timed like the roofline leg (traced correlate launch, L2 flushed,
+    mean of 'steps'): the 100 ms request, and 100 ms at fs = N kHz with 1 ms
+    blocks for N = 2048 ... 16384.  Variant codes as gnss_autotune takes them;
+    the default of each size is restored afterwards."""
+    import siggen
+    TM, CL, ST, OCC = 0x400, 0x200, 0x100, 0x800
+    K2, M2 = 1 << 12, 1 << 14
+    cand = [16, 32, 8, 16 | ST, 16 | CL, 32 | CL, 16 | TM, 16 | TM | K2, 16 | TM | M2, 16 | TM | K2 | M2,
+            16 | TM | OCC, 32 | TM, 32 | TM | M2]
+
+    def time_plan(plan, raw, n):
+        out = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+        default = plan.xcorr_variant()
+        res = {}
+        for code in cand:
+            try:
+                plan.autotune(code)
+            except g.GnssError:
+                continue
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    plan.acquire_device(raw, n, out, stream=stream)
+            torch.cuda.synchronize()
+            tev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+            with torch.cuda.stream(stream):
+                for k in range(steps):
+                    flush.fill_(float(k))
+                    plan.acquire_device_traced(raw, n, out, tev[k], stream=stream)
+            torch.cuda.synchronize()
+            res[hex(code)] = statistics.mean(e[2].elapsed_time(e[3]) for e in tev)
+        plan.autotune(default)
+        return {"default": hex(default), "correlate_ms": res}
+
+    out = {"weak_100ms": time_plan(g.Plan.for_recording(rec),
+                                   torch.from_numpy(np.ascontiguousarray(rec.raw)).cuda(), rec.n_samples)}
+    for N in (2048, 4096, 8192, 16384):
+        fs, n = N * 1000, 100 * N
+        rng = np.random.default_rng(1309005210 + N)
+        sats = [siggen.Sat(prn=9, cn0_dbhz=45.0, dopp_hz=-1750.0, code_phase_chips=100.7, carrier_phase=0.3,
+                           bit_edge_ms=3.0)]
+        li, lq = siggen.quantize_2bit(siggen.synthesize(rng, fs, n, sats), sats, fs)
+        raw = torch.from_numpy(np.ascontiguousarray(siggen.pack(li, lq, siggen.FMT_2BIT_IQ))).cuda()
+        plan = g.Plan(fs, 1, -10000, 250, 81, prns=range(1, 33), fmt=siggen.FMT_2BIT_IQ)
+        out[str(N)] = time_plan(plan, raw, n)
+        plan.close()
+    return out
+
+
 def run_serving_curve(g, serve, rates, seconds, bound_ms, seed=1309005205):
     """Latency against offered load through gnss_submit / gnss_poll: one
     server (plans and code spectra made resident once, before timing) takes
@@ -837,6 +887,8 @@ def run_ours(args):
         line["zoom_vs_refine"] = run_zoom_vs_refine(g, torch, stream)
     if not args.no_sizes:
         line["fft_sizes"] = run_fft_sizes(g, torch, stream, flush, steps=5, peak_tflops=peak_tflops)
+    if args.variants:
+        line["variants"] = run_variants(g, torch, rec, stream, flush)
     if ref_rec is not None:
         line["refine"] = run_refine(g, torch, ref_rec, stream, steps=10, peak_tflops=peak_tflops)
     if trk_rec is not None:
@@ -1020,6 +1072,8 @@ def main():
     ap.add_argument("--no-track", action="store_true")
     ap.add_argument("--no-zoom", action="store_true")
     ap.add_argument("--no-sizes", action="store_true", help="skip the correlate at N = 2048 ... 16384")
+    ap.add_argument("--variants", action="store_true",
+                    help="also time every correlate variant the GPU accepts (100 ms request, N = 2048 ... 16384)")
     ap.add_argument("--batch-requests", type=int, default=256)
     ap.add_argument("--serve-rates", default="50,100,150,175,200,250",
                     help="offered request rates of the serving curve (requests/s)")
