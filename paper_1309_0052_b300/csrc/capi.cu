@@ -295,6 +295,9 @@ gnss_status gnss_plan_create(const gnss_plan_desc* desc, gnss_plan** out) {
   if (p->C >= p->D) p->C = 0;  // nothing shared: keep one spectrum per bin
   cudaError_t e = cudaGetDevice(&p->device);
   if (e == cudaSuccess) e = ensure_fold_roots();
+  // settle the correlate variant of this FFT size on this device now (its
+  // default asks the runtime for occupancies), outside any later stream capture
+  if (e == cudaSuccess) (void)xcorr_variant(N);
   cudaStream_t st = nullptr;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_prns, sizeof(int) * p->P);

@@ -672,9 +672,12 @@ uint32_t xcorr_ctas(int code, int P, int D) {
 // while it holds columns.)
 template <typename Kern>
 static bool tm_cols_fit(Kern k, int T, size_t smem, int cols) {
-  if (set_smem(k, smem) != cudaSuccess) return false;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, T, smem) != cudaSuccess) return false;
+  if (set_smem(k, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, T, smem) != cudaSuccess) {
+    cudaGetLastError();  // a refused shape leaves no error for a later launch check to pick up
+    return false;
+  }
   return occ >= 1 && occ * cols <= 512;
 }
 
