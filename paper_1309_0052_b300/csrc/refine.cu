@@ -123,7 +123,7 @@ struct EvalPoint {
   float tf;       // and its fraction + 1/2, in [0.5, 1.5)
 };
 
-template <int T, int FMT, bool GRAD>
+template <int T, int FMT, bool GRAD, bool W32>
 __device__ EvalOut evaluate(const RefineJob& J, const CodeBits& cb, const Span& sp, double f, double tau, float* red,
                             EvalPoint* pt) {
   if (threadIdx.x == 0) {
@@ -149,41 +149,52 @@ __device__ EvalOut evaluate(const RefineJob& J, const CodeBits& cb, const Span& 
   sincospif(-2.f * ph0, &s0, &c0);
   float2 car = make_float2(c0, s0);
   const float2 rot = pt->rot;
-  // code position: n * 1023 = q N + rem; u = (q - ti) + (rem / N - tf - 1/2)
+  // code position: n * 1023 = q N + rem; u = (q - ti) + (rem / N - tf - 1/2).
+  // The thread's first sample takes it from the exact integers; each next
+  // sample advances it by 1023 / N chips: k by the integer part, the weight a
+  // by the fraction (a multiple of 1 / N, N a power of two), carrying into k.
   const int ti = pt->ti;
   const float tf = pt->tf;
   const float invN = 1.f / (float)J.N;
-  int q = sp.q0;
-  int rem = sp.rem0;
-  const float half_L = 0.5f * (float)J.L;
+  const int istep = 1023 / J.N;                              // whole chips per sample
+  const float fstep = (float)(1023 - istep * J.N) * invN;  // and the fraction, exact
+  const float u0 = fmaf((float)sp.rem0, invN, -tf);          // in (-1.5, 0.5)
+  const float fl0 = floorf(u0);
+  int k = sp.q0 - ti + (int)fl0;  // chip of the sample (before reduction modulo 1023)
+  float a = u0 - fl0;             // its interpolation weight, in [0, 1)
+  float nn = (float)n0 - 0.5f * (float)J.L;  // n - L/2, exact in FP32 (|n| < 2^24)
   float zr = 0.f, zi = 0.f, fr = 0.f, fi = 0.f, tr = 0.f, tii = 0.f;
   for (int base = 0; base < chunk; base += 8) {
     float xi[8], xq[8];
     load8<FMT>(J.samples, n0 + base, xi, xq);
-    // chips of the group: the position only grows, by under 32 chips over 8
-    // samples (N >= 256), so one 64-bit window from the group's first chip
-    // serves all of them (and each next chip)
-    const int kf = q - ti + (int)floorf(fmaf((float)rem, invN, -tf));
+    // chips of the group: the position only grows, by at most 8 (istep + 1)
+    // chips over 8 samples, so one window from the group's first chip serves
+    // all of them and each next chip: 32 bits for N >= 512 (under 18 chips),
+    // 64 for N = 256 (under 33)
+    const int kf = k;
     int km = kf % 1023;
     km += (km < 0) ? 1023 : 0;
     const uint32_t lo = __funnelshift_r(cb.w[km >> 5], cb.w[(km >> 5) + 1], km & 31);
-    const uint32_t hi = __funnelshift_r(cb.w[(km >> 5) + 1], cb.w[(km >> 5) + 2], km & 31);
-    const uint64_t win = ((uint64_t)hi << 32) | lo;
+    uint32_t hi = 0;
+    if constexpr (!W32) hi = __funnelshift_r(cb.w[(km >> 5) + 1], cb.w[(km >> 5) + 2], km & 31);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       // wiped sample w = x e^{-j theta}
       const float wr = fmaf(xi[e], car.x, -xq[e] * car.y);
       const float wi = fmaf(xi[e], car.y, xq[e] * car.x);
-      // interpolated chip
-      float ufrac = fmaf((float)rem, invN, -tf);  // in (-1.5, 0.5)
-      int k = q - ti;
-      const float fl = floorf(ufrac);
-      k += (int)fl;
-      const float a = ufrac - fl;
+      // interpolated chip: the sign bits of chips k and k + 1 as +-1
       const uint32_t rel = (uint32_t)(k - kf);
-      const uint32_t b0 = (uint32_t)(win >> rel) & 1u, b1 = (uint32_t)(win >> (rel + 1u)) & 1u;
-      const float c0v = __int_as_float(0x3f800000 | (int)(b0 << 31));  // +-1
-      const float c1v = __int_as_float(0x3f800000 | (int)(b1 << 31));
+      uint32_t s0, s1;
+      if constexpr (W32) {
+        s0 = (lo << (31u - rel)) & 0x80000000u;
+        s1 = (lo << (30u - rel)) & 0x80000000u;
+      } else {
+        const uint64_t win = ((uint64_t)hi << 32) | lo;
+        s0 = (uint32_t)((win >> rel) & 1u) << 31;
+        s1 = (uint32_t)((win >> (rel + 1u)) & 1u) << 31;
+      }
+      const float c0v = __int_as_float(0x3f800000 | (int)s0);  // +-1
+      const float c1v = __int_as_float(0x3f800000 | (int)s1);
       const float sl = c1v - c0v;
       const float ct = fmaf(a, sl, c0v);
       zr = fmaf(wr, ct, zr);
@@ -192,17 +203,18 @@ __device__ EvalOut evaluate(const RefineJob& J, const CodeBits& cb, const Span& 
         // sum (n - L/2) w ctilde: the L/2 z part of sum n w ctilde adds
         // 2 Re(conj(z) (-j 2 pi L/2 / fs) z) = 0 to dP/df, and centring n
         // keeps the FP32 sum free of that cancellation
-        const float nn = (float)(n0 + base + e) - half_L;
         fr = fmaf(nn * wr, ct, fr);
         fi = fmaf(nn * wi, ct, fi);
         tr = fmaf(-wr, sl, tr);      // sum -w slope
         tii = fmaf(-wi, sl, tii);
+        nn += 1.f;
       }
       car = c_mul(car, rot);
-      rem += 1023;
-      if (rem >= J.N) {
-        rem -= J.N;
-        ++q;
+      a += fstep;
+      k += istep;
+      if (a >= 1.f) {
+        a -= 1.f;
+        ++k;
       }
     }
   }
@@ -249,7 +261,7 @@ __device__ __forceinline__ void load_chips(const RefineJob& J, int prn, CodeBits
 }
 
 // K6/K7: P and gradient for candidate blockIdx.x.
-template <int T, int FMT>
+template <int T, int FMT, bool W32>
 __global__ void __launch_bounds__(T) k_refine_eval(RefineJob J, const int* __restrict__ prn, const double* __restrict__ f,
                                                   const double* __restrict__ tau, float* __restrict__ P,
                                                   float* __restrict__ dPdf, float* __restrict__ dPdtau) {
@@ -258,7 +270,7 @@ __global__ void __launch_bounds__(T) k_refine_eval(RefineJob J, const int* __res
   load_chips<T>(J, prn[blockIdx.x], chips);
   __shared__ EvalPoint pt;
   const Span sp(J, T);
-  const EvalOut o = evaluate<T, FMT, true>(J, chips, sp, f[blockIdx.x], tau[blockIdx.x], red, &pt);
+  const EvalOut o = evaluate<T, FMT, true, W32>(J, chips, sp, f[blockIdx.x], tau[blockIdx.x], red, &pt);
   if (threadIdx.x == 0) {
     P[blockIdx.x] = o.P;
     if (dPdf) dPdf[blockIdx.x] = o.gf;
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__(T) k_refine_eval(RefineJob J, const int* __res
 // s_tau < 1e-5 chip, stuck (status 1) when neither coordinate moved, or
 // max_iter (status 2).  Control flow is uniform over the CTA because every
 // decision uses block-reduced values.
-template <int T, int FMT>
+template <int T, int FMT, bool W32>
 __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate* __restrict__ cands, int max_iter,
                                              double search_hz, gnss_refined* __restrict__ out) {
   __shared__ CodeBits chips;
@@ -303,11 +315,11 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
   unsigned n_p = 0, n_pg = 0;
   auto eval_p = [&](double ff, double tt, float* rd, EvalPoint* p) {
     ++n_p;
-    return evaluate<T, FMT, false>(J, chips, sp, ff, tt, rd, p);
+    return evaluate<T, FMT, false, W32>(J, chips, sp, ff, tt, rd, p);
   };
   auto eval_pg = [&](double ff, double tt, float* rd, EvalPoint* p) {
     ++n_pg;
-    return evaluate<T, FMT, true>(J, chips, sp, ff, tt, rd, p);
+    return evaluate<T, FMT, true, W32>(J, chips, sp, ff, tt, rd, p);
   };
   if (search_hz > 0.0) {
     const double d = J.fs / (2.0 * (double)J.L);
@@ -406,14 +418,22 @@ static constexpr int kRefineThreads = 256;
 template <int FMT>
 static cudaError_t refine_eval_fmt(const RefineJob& J, int n, const int* prn, const double* f, const double* tau,
                                    float* P, float* dPdf, float* dPdtau, cudaStream_t s) {
-  k_refine_eval<kRefineThreads, FMT><<<n, kRefineThreads, 0, s>>>(J, prn, f, tau, P, dPdf, dPdtau);
+  // 32-bit chip windows when N >= 512 (under 18 chips per group of 8 samples)
+  if (J.N >= 512)
+    k_refine_eval<kRefineThreads, FMT, true><<<n, kRefineThreads, 0, s>>>(J, prn, f, tau, P, dPdf, dPdtau);
+  else
+    k_refine_eval<kRefineThreads, FMT, false><<<n, kRefineThreads, 0, s>>>(J, prn, f, tau, P, dPdf, dPdtau);
   return cudaGetLastError();
 }
 
 template <int FMT>
 static cudaError_t refine_fmt(const RefineJob& J, int n, const gnss_candidate* cands, int max_iter,
                               double search_hz, gnss_refined* out, cudaStream_t s) {
-  k_refine<kRefineThreads, FMT><<<n, kRefineThreads, 0, s>>>(J, cands, max_iter, search_hz, out);
+  // 32-bit chip windows when N >= 512 (under 18 chips per group of 8 samples)
+  if (J.N >= 512)
+    k_refine<kRefineThreads, FMT, true><<<n, kRefineThreads, 0, s>>>(J, cands, max_iter, search_hz, out);
+  else
+    k_refine<kRefineThreads, FMT, false><<<n, kRefineThreads, 0, s>>>(J, cands, max_iter, search_hz, out);
   return cudaGetLastError();
 }
 
