@@ -120,6 +120,10 @@ typedef struct {
 #define GNSS_DET_STAGE_TIMEOUT 0x01u /* a bounded wait of the staged correlate variant gave up in this call: its
                                         CTA read the spectra from global memory instead and the results are
                                         complete, but a copy may have outlived its CTA (see gnss_autotune) */
+#define GNSS_DET_WAIT_TIMEOUT 0x02u  /* a bounded wait between the warps of a correlate CTA (the shared-memory
+                                        exchange buffer's release) gave up in this call: the CTA went on
+                                        without it and the call's records and surfaces are not valid */
+#define GNSS_DET_TIMEOUTS (GNSS_DET_STAGE_TIMEOUT | GNSS_DET_WAIT_TIMEOUT)
 typedef struct {
   uint8_t prn;
   uint8_t detected;
@@ -199,9 +203,9 @@ GNSS_API size_t gnss_recording_bytes(uint32_t format, size_t n_samples);
  *                     the call returns)
  * Errors: GNSS_EINVAL (n_samples < L, misaligned device pointer, NULL
  * arguments), GNSS_ENOMEM, GNSS_ECUDA; with a NULL stream also
- * GNSS_ETIMEOUT when a bounded wait of the staged correlate variant gave up
- * during this call (the records are complete and carry
- * GNSS_DET_STAGE_TIMEOUT; every entry point reports such a wait through the
+ * GNSS_ETIMEOUT when a bounded wait inside the correlate kernel gave up
+ * during this call (the records carry GNSS_DET_STAGE_TIMEOUT or
+ * GNSS_DET_WAIT_TIMEOUT; every entry point reports such a wait through the
  * flags of its records, and the server fails the request's ticket with
  * GNSS_ETIMEOUT, keeping its records). */
 GNSS_API gnss_status gnss_acquire(gnss_plan* plan, const void* samples, size_t n_samples, int samples_on_device,

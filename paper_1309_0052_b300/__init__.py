@@ -117,6 +117,7 @@ _SIGS = {
     "gnss_autotune": ([_P, C.c_uint32, _P], _st),
     "gnss_probe_ffma": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], _st),
     "gnss_testing_set_stage_wait_limit": ([C.c_uint32, _P], _st),
+    "gnss_testing_set_buf_wait_limit": ([C.c_uint32, _P], _st),
     "gnss_last_error": ([], C.c_char_p),
 }
 _lib = None
@@ -495,7 +496,16 @@ def set_stage_wait_limit(iters: int, stream=None) -> None:
     check(load().gnss_testing_set_stage_wait_limit(iters, _stream_ptr(stream)), "gnss_testing_set_stage_wait_limit")
 
 
+def set_buf_wait_limit(iters: int, stream=None) -> None:
+    """gnss_testing_set_buf_wait_limit (a testing hook): polls of each wait of
+    the 4096-point occupancy form for its exchange buffer's release (0: every
+    wait gives up at once and the call's records are flagged WAIT_TIMEOUT;
+    the default is 4194304)."""
+    check(load().gnss_testing_set_buf_wait_limit(iters, _stream_ptr(stream)), "gnss_testing_set_buf_wait_limit")
+
+
 STAGE_TIMEOUT = 0x01  # GNSS_DET_STAGE_TIMEOUT: a record's flags bit
+WAIT_TIMEOUT = 0x02  # GNSS_DET_WAIT_TIMEOUT: a record's flags bit (records not valid)
 STAGE_WAIT_DEFAULT = 1 << 22
 
 

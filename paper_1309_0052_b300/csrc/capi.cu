@@ -170,9 +170,12 @@ static gnss_status acquire_impl(gnss_plan* plan, const void* samples, size_t n_s
     e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     for (int p = 0; p < s.P; ++p)
-      if (out_host[p].flags & GNSS_DET_STAGE_TIMEOUT)
-        return fail(GNSS_ETIMEOUT, "a bounded wait of the staged correlate kernel gave up (records complete, "
-                                   "flagged GNSS_DET_STAGE_TIMEOUT)");
+      if (out_host[p].flags & GNSS_DET_TIMEOUTS)
+        return fail(GNSS_ETIMEOUT, (out_host[p].flags & GNSS_DET_WAIT_TIMEOUT)
+                                       ? "a bounded wait between the warps of a correlate CTA gave up (records "
+                                         "flagged GNSS_DET_WAIT_TIMEOUT, not valid)"
+                                       : "a bounded wait of the staged correlate kernel gave up (records complete, "
+                                         "flagged GNSS_DET_STAGE_TIMEOUT)");
   }
   return GNSS_OK;
 }
@@ -706,6 +709,12 @@ gnss_status gnss_batch_graph_destroy(gnss_batch_graph* g) {
 gnss_status gnss_testing_set_stage_wait_limit(uint32_t iters, void* stream) {
   const cudaError_t e = set_stage_wait_limit(iters, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gnss_testing_set_stage_wait_limit");
+  return GNSS_OK;
+}
+
+gnss_status gnss_testing_set_buf_wait_limit(uint32_t iters, void* stream) {
+  const cudaError_t e = set_buf_wait_limit(iters, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gnss_testing_set_buf_wait_limit");
   return GNSS_OK;
 }
 

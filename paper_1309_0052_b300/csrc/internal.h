@@ -150,6 +150,7 @@ int xcorr_default_e(int N);
 bool xcorr_valid_e(int N, int code);
 // Iterations a staged-correlate wait polls before it gives up (testing).
 cudaError_t set_stage_wait_limit(unsigned iters, cudaStream_t stream);
+cudaError_t set_buf_wait_limit(unsigned iters, cudaStream_t stream);
 void set_xcorr_variant(int N, int E);
 // Correlate CTAs of one request (P PRNs, D bins) under variant 'code': one
 // per (PRN, bin), or per group of PRNs and bins (GNSS_TUNE_TMEM shapes).

@@ -240,7 +240,7 @@ void CUDART_CB on_batch_done(void* arg) {
         r.state = St::Done;
         r.status = GNSS_OK;
         for (const gnss_detection& d : r.result)
-          if (d.flags & GNSS_DET_STAGE_TIMEOUT) r.status = GNSS_ETIMEOUT;  // records kept, call reported
+          if (d.flags & GNSS_DET_TIMEOUTS) r.status = GNSS_ETIMEOUT;  // records kept, call reported
         if (r.status == GNSS_OK) srv->stats.completed++;
         else srv->stats.failed++;
       }

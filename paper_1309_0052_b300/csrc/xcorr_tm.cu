@@ -15,8 +15,9 @@
 //     the current block's products are formed, so its L2 latency passes
 //     under the current block's transform (16 elements per thread);
 //   - where the registers cannot also hold the non-coherent sums (two PRNs
-//     per CTA, or 32 elements per thread at N = 16384) those live in TMEM
-//     too (tcgen05.ld before the transform, add and tcgen05.st after it).
+//     per CTA, 32 elements per thread at N = 16384, or the occupancy form)
+//     those live in TMEM too (tcgen05.ld, add and tcgen05.st around each
+//     block's |.|^2).
 // A CTA can take K PRNs of one Doppler bin (one Y load feeds K products and
 // K transforms) and M bins one after another (the code spectra stay in
 // TMEM across bins).
@@ -174,11 +175,16 @@ struct TmShape {
   static_assert(T >= 32, "tcgen05.ld/st run on whole warps");
   static constexpr int WARPS = T / 32;
   static constexpr int SLOTS = WARPS >= 4 ? WARPS / 4 : 1;  // warps sharing a lane quarter
-  // The occupancy form (O): one more CTA per SM of 128 threads or more
-  // (registers capped at 80 for three 256-thread CTAs, six of 128), the
-  // sums in TMEM and no register prefetch, so more warps hide latency.
-  static constexpr int MINB = O ? (T <= 256 ? 768 / T : 1) : X::MINB;
-  static constexpr size_t smem = (X::DB || CL ? 2 : 1) * X::buf_bytes;  // exchange buffers only
+  // The occupancy form (O): more CTAs per SM, so more warps hide latency --
+  // the sums in TMEM, no register prefetch, and registers capped at 80 for
+  // three 256-thread CTAs (six of 128).  At 4096 (ONEBUF) four 256-thread
+  // CTAs at 64 registers, each with ONE exchange buffer (4 x 35 KB of shared
+  // memory, 4 x 128 TMEM columns): the buffer's reuse by the next transform
+  // waits on an mbarrier that every thread arrives on after its last read
+  // (fft4096_cl_tmtw), so the wait falls a whole pass after the arrivals.
+  static constexpr bool ONEBUF = O && CL && N == 4096;
+  static constexpr int MINB = O ? (ONEBUF ? 4 : T <= 256 ? 768 / T : 1) : X::MINB;
+  static constexpr size_t smem = ((X::DB || CL) && !ONEBUF ? 2 : 1) * X::buf_bytes;  // exchange buffers only
   template <int K>
   struct Cols {
     // sums in registers with one PRN of 16 elements; else E TMEM columns per PRN
@@ -294,12 +300,65 @@ __device__ __forceinline__ void tw_to_tmem(const TwBase16& a, const TwBase16& b,
   tm_st16(ta, w);
 }
 
-__device__ __forceinline__ void fft4096_cl_tmtw(float2 (&v)[16], int t, float2* buf, uint32_t ta_tw) {
+//
+// With one exchange buffer per CTA (TmShape::ONEBUF) the first-pass stores of
+// a transform must not land while another warp still reads the previous
+// transform's classes.  An mbarrier of T arrivals per transform orders them:
+// each thread arrives right after its last read of the buffer (the class
+// gathers before the NS = 256 pass) and waits for that phase only before its
+// next first-pass stores, so the wait spans the NS = 256 pass, the sums,
+// the next block's loads and products and the next first pass.  Each wait
+// polls at most g_buf_wait_limit times; one that gives up marks the call's
+// status word (GNSS_DET_WAIT_TIMEOUT: the call's results are not valid) and
+// goes on, so the CTA still finishes and frees its TMEM.  (The limit is
+// lowered only by the testing entry point: at 0 every wait gives up at once
+// and the CTA's warps race on the buffer -- in bounds, results flagged.)
+__device__ unsigned g_buf_wait_limit = 1u << 22;
+
+struct BufRelease {
+  uint64_t* bar;     // the CTA's mbarrier (shared memory), T arrivals per phase
+  unsigned* status;  // the call's status word
+  uint32_t n;        // transforms this thread has run
+};
+
+__device__ __forceinline__ uint32_t tm_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void buf_release_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tm_smem_u32(bar)), "r"(count) : "memory");
+}
+
+// release: this thread's reads of the buffer are ordered before the arrival
+__device__ __forceinline__ void buf_release_arrive(BufRelease& rel) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tm_smem_u32(rel.bar)) : "memory");
+  ++rel.n;
+}
+
+// acquire: every thread's reads of the previous transform precede this
+// thread's stores (no wait before a CTA's first transform)
+__device__ __forceinline__ void buf_release_wait(const BufRelease& rel) {
+  if (rel.n == 0) return;
+  const uint32_t parity = (rel.n - 1) & 1u;
+  const unsigned limit = g_buf_wait_limit;
+  for (unsigned it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(tm_smem_u32(rel.bar)), "r"(parity)
+        : "memory");
+    if (done) return;
+  }
+  atomicOr(rel.status, (unsigned)GNSS_DET_WAIT_TIMEOUT);
+}
+
+template <bool ONEBUF>
+__device__ __forceinline__ void fft4096_cl_tmtw(float2 (&v)[16], int t, float2* buf, uint32_t ta_tw, BufRelease& rel) {
   constexpr int N = 4096, T = N / 16;
   {
     FftTw<N, 16, true, 1> none;  // pass 1 (NS = 1) takes no twiddles
     pass_compute_tw<N, 16, 16, 1, true>(v, none);
   }
+  if constexpr (ONEBUF) buf_release_wait(rel);
   {
     float2* b = buf + pad_cl(16 * t);
 #pragma unroll
@@ -331,6 +390,7 @@ __device__ __forceinline__ void fft4096_cl_tmtw(float2 (&v)[16], int t, float2* 
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = g[cl_off(T * r)];
+  if constexpr (ONEBUF) buf_release_arrive(rel);  // the last read of the buffer in this transform
   {
     tm_wait_ld8(w);
     FftTw<N, 16, true, 256> tw;
@@ -345,8 +405,9 @@ __device__ __forceinline__ void fft4096_cl_tmtw(float2 (&v)[16], int t, float2* 
 // runs its blocks set by set (with half-bit sets the even blocks, then the
 // odd ones); within a block the K PRNs share the Y that was loaded during the
 // previous block.  The sums stay in registers with one PRN of 16 elements
-// per thread; otherwise they live in TMEM (with 16 per thread the block's
-// sums are fetched before its transform and updated after it).
+// per thread (except in the occupancy form); otherwise they live in TMEM
+// (with two PRNs of 16 per thread the block's sums are fetched before its
+// transform, in the occupancy form after it, and updated after it).
 // ---------------------------------------------------------------------------
 template <int N, int E, bool HALF, int K, int M, bool O>
 __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float2* sm) {
@@ -356,7 +417,7 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
   constexpr int T = Sh::T, S = HALF ? 2 : 1;
   constexpr bool CL = Sh::CL, RACC = Cl::acc_regs;
   float2* buf0 = sm;
-  float2* buf1 = (X::DB || CL) ? sm + X::buf_bytes / sizeof(float2) : sm;
+  float2* buf1 = ((X::DB || CL) && !Sh::ONEBUF) ? sm + X::buf_bytes / sizeof(float2) : sm;
   __shared__ float s_val[32];
   __shared__ uint32_t s_idx[32];
   __shared__ uint32_t s_tmem;
@@ -375,6 +436,11 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
   // Columns are taken only now: a CTA never holds TMEM while it waits for
   // another kernel, and between here and the release below it waits for
   // nothing, so an allocation can at worst wait for CTAs that run on.
+  __shared__ uint64_t s_release;
+  BufRelease rel{&s_release, a.counters + a.P, 0};
+  if constexpr (Sh::ONEBUF) {
+    if (j == 0) buf_release_init(&s_release, (unsigned)T);  // visible after the barrier below
+  }
   if (warp == 0) tm_alloc<Cl::alloc>(&s_tmem);
   tm_fence_before();
   __syncthreads();
@@ -490,18 +556,8 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
             tm_load_row<N, E>(v, yb, js);
             tm_product<E>(tq, v, v);
           }
-          float s16[RACC || E != 16 ? 1 : 16];
-          if constexpr (!RACC && E == 16) {
-            if (t > 0) {
-              tm_wait_st();
-              tm_ld16(tsum, s16);
-            } else {
-#pragma unroll
-              for (int r = 0; r < 16; ++r) s16[r] = 0.f;
-            }
-          }
           if constexpr (Cl::tw_tmem) {
-            fft4096_cl_tmtw(v, j, phase ? buf1 : buf0, ttw);
+            fft4096_cl_tmtw<Sh::ONEBUF>(v, j, phase ? buf1 : buf0, ttw, rel);
             phase ^= 1;
           } else if constexpr (CL) {
             fft_class_local<N, true>(v, j, phase ? buf1 : buf0, tw);
@@ -514,7 +570,17 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
           if constexpr (RACC) {
             add_power<E>(racc, v);
           } else if constexpr (E == 16) {
-            tm_wait_ld16(s16);
+            // the sums are fetched only now: 16 registers fewer live through
+            // the transform (the occupancy form runs at 64 or 80 registers)
+            float s16[16];
+            if (t > 0) {
+              tm_wait_st();
+              tm_ld16(tsum, s16);
+              tm_wait_ld16(s16);
+            } else {
+#pragma unroll
+              for (int r = 0; r < 16; ++r) s16[r] = 0.f;
+            }
             add_power<16>(s16, v);
             tm_st16(tsum, s16);
           } else {
@@ -656,6 +722,13 @@ __global__ void __launch_bounds__(TmShape<N, E, O>::T, TmShape<N, E, O>::MINB)
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+cudaError_t set_buf_wait_limit(unsigned iters, cudaStream_t stream) {
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_buf_wait_limit, &iters, sizeof(unsigned), 0, cudaMemcpyHostToDevice,
+                                          stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(stream);
+}
+
 int xcorr_tm_prns(int code) { return (code & (int)GNSS_TUNE_TMEM) ? ((code >> 12) & 3) + 1 : 1; }
 int xcorr_tm_bins(int code) { return (code & (int)GNSS_TUNE_TMEM) ? ((code >> 14) & 3) + 1 : 1; }
 

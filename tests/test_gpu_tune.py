@@ -432,3 +432,44 @@ def test_staged_wait_gives_up_safely(g):
         np.testing.assert_array_equal(again["peak"], ref["peak"])
     finally:
         plan.autotune(_default(4096))
+
+
+def test_buffer_release_wait_gives_up_safely(g):
+    """The 4096-point occupancy form keeps one exchange buffer per CTA; the
+    next transform's stores wait (bounded) for every warp's release of it.
+    With the testing hook every such wait gives up at once: the warps then
+    race on the buffer (shared memory, in bounds), and every call reports it
+    -- the synchronous call returns GNSS_ETIMEOUT, the device-resident and
+    batched calls flag every record with GNSS_DET_WAIT_TIMEOUT.  With the
+    limit back, the next call carries no flag and equals the reference."""
+    raw_np, n = _recording(4096, 1, 5, siggen.FMT_2BIT_IQ, 4096)
+    plan = g.Plan(4_096_000, 1, -3000, 250, 9, prns=[3, 9, 30], half_bit=True, fmt=siggen.FMT_2BIT_IQ)
+    raw = torch.from_numpy(np.ascontiguousarray(raw_np)).cuda()
+    occ = 16 | TMEM | OCC
+    try:
+        plan.autotune(occ)
+        ref = plan.acquire(raw, n)
+        assert not (ref["flags"] & (g.WAIT_TIMEOUT | g.STAGE_TIMEOUT)).any()
+        g.set_buf_wait_limit(0)
+        try:
+            out = np.zeros(plan.n_prn, g.DETECTION_DTYPE)
+            with pytest.raises(g.GnssError) as e:
+                plan.acquire(raw, n, out=out)
+            assert e.value.status == g.ETIMEOUT
+            assert (out["flags"] & g.WAIT_TIMEOUT).all()
+            od = torch.zeros(plan.n_prn * 28, dtype=torch.uint8, device="cuda")
+            plan.acquire_device(raw, n, od)
+            torch.cuda.synchronize()
+            assert (g.detections_from_bytes(od.cpu().numpy())["flags"] & g.WAIT_TIMEOUT).all()
+            ob = torch.zeros_like(od)
+            g.acquire_batch([(plan, raw, n, ob, None)])
+            torch.cuda.synchronize()
+            assert (g.detections_from_bytes(ob.cpu().numpy())["flags"] & g.WAIT_TIMEOUT).all()
+        finally:
+            g.set_buf_wait_limit(g.STAGE_WAIT_DEFAULT)
+        again = plan.acquire(raw, n)
+        assert not (again["flags"] & g.WAIT_TIMEOUT).any()
+        for f in ("prn", "detected", "set", "dopp_bin", "code_phase", "peak", "second", "ratio"):
+            np.testing.assert_array_equal(again[f], ref[f])
+    finally:
+        plan.autotune(_default(4096))
