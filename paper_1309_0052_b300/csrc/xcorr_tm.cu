@@ -177,14 +177,19 @@ struct TmShape {
   static constexpr int SLOTS = WARPS >= 4 ? WARPS / 4 : 1;  // warps sharing a lane quarter
   // The occupancy form (O): more CTAs per SM, so more warps hide latency --
   // the sums in TMEM, no register prefetch, and registers capped at 80 for
-  // three 256-thread CTAs (six of 128).  At 4096 (ONEBUF) four 256-thread
-  // CTAs at 64 registers, each with ONE exchange buffer (4 x 35 KB of shared
-  // memory, 4 x 128 TMEM columns): the buffer's reuse by the next transform
-  // waits on an mbarrier that every thread arrives on after its last read
-  // (fft4096_cl_tmtw), so the wait falls a whole pass after the arrivals.
-  static constexpr bool ONEBUF = O && CL && N == 4096;
-  static constexpr int MINB = O ? (ONEBUF ? 4 : T <= 256 ? 768 / T : 1) : X::MINB;
-  static constexpr size_t smem = ((X::DB || CL) && !ONEBUF ? 2 : 1) * X::buf_bytes;  // exchange buffers only
+  // three 256-thread CTAs (six of 128).  With the class-local schedule
+  // (ONEBUF) 64 registers and ONE exchange buffer per CTA: four 256-thread
+  // CTAs at 4096 (4 x 35 KB of shared memory, 4 x 128 TMEM columns), two
+  // 512-thread CTAs at 8192 (2 x (70 + 32) KB: the buffer and the lane-pair
+  // pass's twiddle table; 2 x 256 TMEM columns).  The buffer's reuse by the
+  // next transform waits on an mbarrier that every thread arrives on after
+  // its last read (fft_cl_tmtw), so the wait falls a whole pass after the
+  // arrivals.
+  static constexpr bool ONEBUF = O && CL;
+  static constexpr int MINB = O ? (ONEBUF ? 65536 / (64 * T) : T <= 256 ? 768 / T : 1) : X::MINB;
+  // lane-pair twiddles of N = 8192: float4 [4][T] (W^(b + 256 i), i < 8)
+  static constexpr size_t lp_bytes = ONEBUF && N == 8192 ? 4 * T * sizeof(float4) : 0;
+  static constexpr size_t smem = ((X::DB || CL) && !ONEBUF ? 2 : 1) * X::buf_bytes + lp_bytes;
   template <int K>
   struct Cols {
     // sums in registers with one PRN of 16 elements; else E TMEM columns per PRN
@@ -193,9 +198,10 @@ struct TmShape {
     // two PRNs run their transforms interleaved instead, see fft_class_local2)
     static constexpr bool prefetch = E == 16 && K == 1 && !O;
     static constexpr int per_prn = acc_regs ? 2 * E : 3 * E;
-    // the occupancy form at 4096 keeps the two twiddled passes' bases (w, w^2,
-    // w^4, w^8 each: 16 floats) in TMEM too, after the PRNs' columns
-    static constexpr bool tw_tmem = O && CL && N == 4096;
+    // the class-local occupancy form keeps the two twiddled radix-16 passes'
+    // bases (w, w^2, w^4, w^8 each: 16 floats) in TMEM too, after the PRNs'
+    // columns
+    static constexpr bool tw_tmem = O && CL;
     static constexpr int tw_cols = tw_tmem ? 16 : 0;
     static constexpr int stride = (K * per_prn + tw_cols + 31) / 32 * 32;  // columns of one warp slot
     static constexpr int alloc = tm_pow2_cols(SLOTS * stride);
@@ -281,10 +287,12 @@ __device__ __forceinline__ void tm_read_sums(uint32_t ta, float (&acc)[E]) {
   }
 }
 
-// The class-local 4096-point inverse transform (fft_class_local, the same
-// passes and operations) with each twiddled pass's bases read from TMEM
-// columns ta .. ta + 8 (pass NS = 16) and ta + 8 .. ta + 16 (NS = 256) right
-// before the pass: 16 registers fewer live through the transform.
+// The class-local 4096- or 8192-point inverse transform (fft_class_local,
+// the same passes and operations) with each twiddled radix-16 pass's bases
+// read from TMEM columns ta .. ta + 8 (pass NS = 16) and ta + 8 .. ta + 16
+// (NS = 256) right before the pass, and at 8192 the lane-pair radix-2 pass's
+// eight twiddles read from this thread's column of a shared-memory table:
+// 16 (32) registers fewer live through the transform.
 __device__ __forceinline__ TwBase16 tw_unpack(const float (&w)[8]) {
   TwBase16 b;
   b.w1 = make_float2(w[0], w[1]);
@@ -351,9 +359,10 @@ __device__ __forceinline__ void buf_release_wait(const BufRelease& rel) {
   atomicOr(rel.status, (unsigned)GNSS_DET_WAIT_TIMEOUT);
 }
 
-template <bool ONEBUF>
-__device__ __forceinline__ void fft4096_cl_tmtw(float2 (&v)[16], int t, float2* buf, uint32_t ta_tw, BufRelease& rel) {
-  constexpr int N = 4096, T = N / 16;
+template <int N, bool ONEBUF>
+__device__ __forceinline__ void fft_cl_tmtw(float2 (&v)[16], int t, float2* buf, uint32_t ta_tw, BufRelease& rel,
+                                            const float4* lp) {
+  constexpr int T = N / 16;
   {
     FftTw<N, 16, true, 1> none;  // pass 1 (NS = 1) takes no twiddles
     pass_compute_tw<N, 16, 16, 1, true>(v, none);
@@ -396,6 +405,16 @@ __device__ __forceinline__ void fft4096_cl_tmtw(float2 (&v)[16], int t, float2* 
     FftTw<N, 16, true, 256> tw;
     tw.tw[0] = tw_unpack(w);
     pass_compute_tw<N, 16, 16, 256, true>(v, tw);
+  }
+  if constexpr (N == 8192) {
+    FftTw<N, 16, true, 4096> lt;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const float4 x = lp[T * h + t];
+      lt.tw[2 * h].a[0] = make_float2(x.x, x.y);
+      lt.tw[2 * h + 1].a[0] = make_float2(x.z, x.w);
+    }
+    lane_pair_radix2<true>(v, jp, lt);
   }
 }
 
@@ -469,6 +488,16 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
   // with the twiddle bases in TMEM: the two twiddled passes' bases, after the PRNs' columns
   const uint32_t ttw = tq + (uint32_t)(K * Cl::per_prn);
   if constexpr (Cl::tw_tmem) tw_to_tmem(tw.next.tw[0], tw.next.next.tw[0], ttw);
+  // and the lane-pair twiddles of N = 8192 into this thread's table column
+  // (read back only by this thread)
+  float4* lp = reinterpret_cast<float4*>(sm + X::buf_bytes / sizeof(float2));
+  if constexpr (Cl::tw_tmem && N == 8192) {
+    const auto& lt = tw.next.next.next;
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+      lp[T * h + j] = make_float4(lt.tw[2 * h].a[0].x, lt.tw[2 * h].a[0].y, lt.tw[2 * h + 1].a[0].x,
+                                  lt.tw[2 * h + 1].a[0].y);
+  }
   tm_wait_st();  // the first block reads them back
   auto bin_at = [&](int u) { return a.bin_order ? __ldg(a.bin_order + u) : u; };
   // bin d's spectrum: its own row, or its class's row read K bins further
@@ -557,7 +586,7 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
             tm_product<E>(tq, v, v);
           }
           if constexpr (Cl::tw_tmem) {
-            fft4096_cl_tmtw<Sh::ONEBUF>(v, j, phase ? buf1 : buf0, ttw, rel);
+            fft_cl_tmtw<N, Sh::ONEBUF>(v, j, phase ? buf1 : buf0, ttw, rel, lp);
             phase ^= 1;
           } else if constexpr (CL) {
             fft_class_local<N, true>(v, j, phase ? buf1 : buf0, tw);
@@ -798,7 +827,7 @@ static cudaError_t tm_launch_batch(const BatchGroup& g, cudaStream_t stream) {
   CALL(4096, 16, 1, 1, false) CALL(4096, 16, 2, 1, false) CALL(4096, 16, 1, 2, false)                      \
   CALL(4096, 16, 2, 2, false) CALL(4096, 16, 1, 1, true)                                                   \
   CALL(8192, 16, 1, 1, false) CALL(8192, 16, 2, 1, false) CALL(8192, 16, 1, 2, false)                      \
-  CALL(8192, 16, 2, 2, false)                                                                              \
+  CALL(8192, 16, 2, 2, false) CALL(8192, 16, 1, 1, true)                                                  \
   CALL(16384, 32, 1, 1, false) CALL(16384, 32, 1, 2, false)
 
 static bool tm_shape(int N, int code, int* E, int* K, int* M, bool* O) {

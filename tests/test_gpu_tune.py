@@ -52,7 +52,7 @@ def _tm_codes(N):
     if e is None:
         return []
     ks = (1, 2) if e == 16 else (1,)
-    occ = [16 | TMEM | OCC] if N in (2048, 4096) else []
+    occ = [16 | TMEM | OCC] if N in (2048, 4096, 8192) else []
     return [e | TMEM | PRNS(k) | BINS(m) for k in ks for m in (1, 2)] + occ
 
 
@@ -72,9 +72,9 @@ def _tm_accepted(g, plan):
 
 
 def _default(N):
-    """The library's default variant at N (the tensor-memory forms at 4096
-    and 16384, which every B300 can hold)."""
-    if N == 4096:
+    """The library's default variant at N (the tensor-memory forms at 4096,
+    8192 and 16384, which every B300 can hold)."""
+    if N in (4096, 8192):
         return 16 | TMEM | OCC
     if N == 16384:
         return 32 | TMEM | BINS(2)
@@ -147,7 +147,7 @@ def test_invalid_shape_rejected(g):
                     (16384, 32 | TMEM | PRNS(2)),   # one PRN per CTA at 16384
                     (4096, 16 | TMEM | PRNS(3)),    # 1 or 2 PRNs per CTA
                     (4096, 16 | TMEM | BINS(4)),    # 1 or 2 bins per CTA
-                    (8192, 16 | TMEM | OCC),        # three CTAs per SM: 2048 and 4096 only
+                    (16384, 32 | TMEM | OCC),       # the occupancy form: 2048, 4096 and 8192 only
                     (4096, 16 | TMEM | OCC | PRNS(2)),  # one PRN and bin per CTA
                     (4096, 16 | OCC),               # a form of the TMEM variant
                     (4096, 16 | TMEM | 0x10000)):   # unknown bits
