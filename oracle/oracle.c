@@ -571,7 +571,11 @@ typedef struct {
  *        kink, so when every trial fails the opposite direction is tried
  *        (taking the first trial that raises P).
  * When every tau trial on both sides, down to s_tau / 2^max_halvings, lowers
- * P, tau sits on the kink of the peak and s_tau is shrunk by that factor.  P and the
+ * P, tau sits on the kink of the peak and s_tau is shrunk by that factor.
+ * An iteration that ends with P no higher than it started (the flat_accept
+ * clause can lower P while the tau step wins it back) halves s_tau: near the
+ * peak the two steps can otherwise trade the last bits of P back and forth
+ * with a tau step that is always accepted and never shrinks.  P and the
  * gradient are re-evaluated after every accepted step.  Stop as converged
  * (status 0) when the Newton step |d_f| is below tol_f Hz and s_tau below
  * tol_tau chip, as stuck (status 1) when neither coordinate moved, or after
@@ -604,6 +608,7 @@ void orc_refine(const double *xr, const double *xi, int64_t L, double fs,
   int it = 0, status = 2;
   for (; it < max_iter; ++it) {
     double move_f = 0.0, move_t = 0.0;
+    const double P_start = P;
     double df = P > 0.0 ? g[0] / (P * curv) : 0.0;
     if (df != 0.0) {
       double alpha = 1.0;
@@ -663,6 +668,7 @@ void orc_refine(const double *xr, const double *xi, int64_t L, double fs,
       /* every trial down to s_tau / 2^20 on both sides lowered P */
       if (!accepted) s_tau = ldexp(s_tau, -max_halvings);
     }
+    if (P <= P_start) s_tau *= 0.5; /* no net gain this iteration */
     if (fabs(df) < tol_f && s_tau < tol_tau) {
       status = 0;
       ++it;

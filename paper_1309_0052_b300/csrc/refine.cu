@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(T) k_refine_eval(RefineJob J, const int* __res
 //     one-sided where samples sit exactly on a kink;
 // re-evaluating P and the gradient after each accepted step; when every tau
 // trial on both sides lowers P, tau sits on the kink of the peak and s_tau
-// shrinks by 2^20.
+// shrinks by 2^20; an iteration that ends with P no higher than it started
+// halves s_tau (near the peak the f step's flat acceptance and the tau step
+// can otherwise trade the last bit of P back and forth forever).
 // Stop: converged (status 0) when the Newton step |d_f| < 1e-3 Hz and
 // s_tau < 1e-5 chip, stuck (status 1) when neither coordinate moved, or
 // max_iter (status 2).  Control flow is uniform over the CTA because every
@@ -339,6 +341,7 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
   int it = 0, status = 2;
   for (; it < max_iter; ++it) {
     double move_f = 0.0, move_t = 0.0;
+    const float P_start = e.P;
     const double df = e.P > 0.f ? (double)e.gf / ((double)e.P * curv) : 0.0;
     if (df != 0.0) {
       double alpha = 1.0;
@@ -390,6 +393,7 @@ __global__ void __launch_bounds__(T) k_refine(RefineJob J, const gnss_candidate*
       }
       if (!accepted) s_tau = ldexp(s_tau, -20);  // every trial on both sides lowered P: on the kink
     }
+    if (e.P <= P_start) s_tau *= 0.5;  // no net gain this iteration
     if (fabs(df) < tol_f && s_tau < tol_tau) {
       status = 0;
       ++it;
