@@ -911,7 +911,8 @@ def xcorr_kernel_name(code, N, half):
     e, sets = code & 0xFF, "half-bit" if half else "one set"
     if code & 0x400:
         k, m = ((code >> 12) & 3) + 1, ((code >> 14) & 3) + 1
-        occ = {2048: "6 CTAs/SM", 4096: "4 CTAs/SM, one buffer", 8192: "2 CTAs/SM, one buffer"}.get(N, "")
+        occ = {2048: "6 CTAs/SM", 4096: "4 CTAs/SM, one buffer", 8192: "2 CTAs/SM, one buffer",
+               16384: "1 CTA/SM of 1024, one buffer"}.get(N, "")
         form = occ if code & 0x800 else ("%d PRN%s, %d bin%s" % (k, "s" * (k > 1), m, "s" * (m > 1)))
         return "k_xcorr_tm<%d,%d,%s,%s>" % (N, e, sets, form)
     if code & 0x200:

@@ -890,17 +890,17 @@ cudaError_t launch_wipe_fft(const AcqShape& s, const uint8_t* d_samples, const i
 static int g_xcorr_e[128][15];
 
 int xcorr_default_e(int N) {
-  // At 4096 and 8192 the tensor-memory occupancy form (the code spectra, sums
-  // and twiddle bases in TMEM, 64 registers, one exchange buffer per CTA:
-  // four CTAs per SM at 4096, 0.211 vs 0.230 ms for the class-local register
-  // form on the 100 ms, 10 ms-block request and 1.84 vs 2.08 ms with 1 ms
-  // blocks; two at 8192, 4.24 vs 4.57 ms for 100 ms at 8.192 MHz, 1 ms
-  // blocks); at 16384 the tensor-memory form with two bins per CTA (11.8 vs
-  // 12.4 ms for 100 ms at 16.384 MHz, 1 ms blocks), each where the GPU can
-  // hold its columns.
+  // At 4096, 8192 and 16384 the tensor-memory occupancy form (the code
+  // spectra, sums and twiddle bases in TMEM, 64 registers, one exchange
+  // buffer per CTA, 32 warps per SM: four CTAs at 4096, 0.211 vs 0.230 ms for
+  // the class-local register form on the 100 ms, 10 ms-block request and
+  // 1.84 vs 2.08 ms with 1 ms blocks; two at 8192, 4.24 vs 4.57 ms for 100 ms
+  // at 8.192 MHz, 1 ms blocks; one of 1024 threads at 16384, 9.59 vs 11.81 ms
+  // for the 32-per-thread form with two bins per CTA, 100 ms at 16.384 MHz),
+  // else at 16384 that two-bin form, each where the GPU can hold its columns.
   const int occ = 16 | (int)GNSS_TUNE_TMEM | (int)GNSS_TUNE_OCC;
   const int tm16384 = 32 | (int)GNSS_TUNE_TMEM | (int)GNSS_TUNE_BINS(2);
-  if ((N == 4096 || N == 8192) && xcorr_tm_valid(N, occ)) return occ;
+  if ((N == 4096 || N == 8192 || N == 16384) && xcorr_tm_valid(N, occ)) return occ;
   if (N == 16384 && xcorr_tm_valid(N, tm16384)) return tm16384;
   if (N == 4096 || N == 8192) return 16 | (int)GNSS_TUNE_CLASS_LOCAL;
   // at 16384 otherwise the 32-per-thread form: faster than the two-CTA split

@@ -587,6 +587,55 @@ struct ClassLocal {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Class-local schedule at N = 16384 (16 per thread, T = 1024 threads): radix
+// 16, 16, 16, then 4.  After the first pass's CTA-wide exchange, class c =
+// J mod 16 (1024 elements) lives on the 64 threads 64 c .. 64 c + 63 (warps
+// 2c, 2c + 1), which run the NS = 16 and NS = 256 passes with one in-place
+// exchange between them guarded by a barrier of those warps.  The NS = 256
+// pass's butterflies J and J + 256 h (h < 4) write exactly the slots that the
+// radix-4 butterflies m = J mod 256 + 256 t read, so the last exchange runs
+// within those four threads -- placed on lanes l, l + 8, l + 16, l + 24 of
+// one warp, it needs only __syncwarp.  The thread of quarter h = J / 256 then
+// runs the radix-4 butterflies m = k + 256 (h + 4 i), i < 4, k = J mod 256,
+// and ends holding X[m + 4096 s] in v[4 i + s] (out_index).
+//
+// Thread position p within the class runs butterfly J = c + 16 i', where i'
+// takes p's bits in the order (0, 5, 1, 2, 4, 3); slot of element i:
+// i + i/16 + i/256 + i/4096.  A CPU check of every access of the schedule
+// (first-pass stores at 16 t + u, class gathers at J + 1024 r, class stores
+// at 256 (J / 16) + J mod 16 + 16 u, quad stores at 4096 h + k + 256 u, quad
+// gathers at k + 256 (h + 4 i) + 4096 s) found each half-warp on 16
+// distinct 8-byte bank pairs, and every offset from a thread's base is a
+// compile-time constant (no carries).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pad_q(int i) { return i + (i >> 4) + (i >> 8) + (i >> 12); }
+// pad_q(x + d) - pad_q(x) for the strides d of the 16384 schedule (no carries)
+__host__ __device__ constexpr int q_off(int d) { return d + d / 16 + d / 256 + d / 4096; }
+
+template <>
+struct ClassLocal<16384> {
+  static constexpr int N = 16384, E = 16, T = N / E, G = 64;
+  static constexpr int smem_elems = N + N / 16 + N / 256 + N / 4096;  // > pad_q(N - 1)
+  __device__ __forceinline__ static int perm(int t) {
+    const int p = t & 63;
+    const int ip = (p & 1) | (((p >> 5) & 1) << 1) | (((p >> 1) & 3) << 2) | (((p >> 4) & 1) << 4) |
+                   (((p >> 3) & 1) << 5);
+    return (t >> 6) + 16 * ip;
+  }
+  // the radix-4 butterfly i of class index jp
+  __device__ __forceinline__ static int quad_m(int jp, int i) { return (jp & 255) + 256 * ((jp >> 8) + 4 * i); }
+  __device__ __forceinline__ static int out_index(int jp, int r) { return quad_m(jp, r >> 2) + 4096 * (r & 3); }
+  template <bool INV>
+  __device__ __forceinline__ static void init_twiddles(FftTw<N, 16, INV>& tw, int jp) {
+    tw.init(jp);  // the radix-16 passes (NS = 16, 256)
+    auto& last = tw.next.next.next;  // NS = 4096, radix 4
+    constexpr float scale = (INV ? 2.f : -2.f) / float(N);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) last.tw[i].init(scale * float(quad_m(jp, i)));
+  }
+};
+
 // The radix-2 pass of N = 8192 across lanes l and l ^ 16 (see above).
 template <bool INV>
 __device__ __forceinline__ void lane_pair_radix2(float2 (&v)[16], int jp, const FftTw<8192, 16, INV, 4096>& tw) {

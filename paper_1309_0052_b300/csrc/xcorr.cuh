@@ -47,7 +47,8 @@ struct Cfg {
 // E = 16: one CTA barrier per block; fft_class_local).
 template <int N, int E, bool ST = false, bool CL = false>
 struct XCfg {
-  static_assert(!CL || ((N == 4096 || N == 8192) && E == 16 && !ST), "class-local schedule: N = 4096 or 8192");
+  static_assert(!CL || ((N == 4096 || N == 8192 || N == 16384) && E == 16 && !ST),
+                "class-local schedule: N = 4096, 8192 or 16384");
   static constexpr int T = N / E;
   static constexpr bool TWC = (E <= 16);                        // twiddle bases cached in registers
   static constexpr size_t buf_bytes =
@@ -178,10 +179,12 @@ __device__ __forceinline__ uint32_t block_min_u32(uint32_t v, uint32_t* s_idx) {
 // phases of a thread are congruent to j modulo 'period'.
 template <int N, int E, bool CL>
 struct PhaseMap {
-  static constexpr bool pairs = CL && N == 8192;
+  // with the lane-pair (8192) or quad (16384) last pass a thread's phases are
+  // all congruent to its class index modulo 256
+  static constexpr bool pairs = CL && (N == 8192 || N == 16384);
   static constexpr int period = pairs ? 256 : N / E;
   __device__ __forceinline__ static int at(int j, int r) {
-    if constexpr (pairs) return ClassLocal<8192>::out_index(j, r);
+    if constexpr (pairs) return ClassLocal<(pairs ? N : 8192)>::out_index(j, r);
     else return j + (N / E) * r;
   }
 };

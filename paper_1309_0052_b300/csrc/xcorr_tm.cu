@@ -169,7 +169,7 @@ __host__ __device__ constexpr int tm_pow2_cols(int c) { return c <= 32 ? 32 : 2 
 
 template <int N, int E, bool O = false>
 struct TmShape {
-  static constexpr bool CL = (N == 4096 || N == 8192) && E == 16;
+  static constexpr bool CL = (N == 4096 || N == 8192 || (N == 16384 && O)) && E == 16;
   using X = XCfg<N, E, false, CL>;
   static constexpr int T = N / E;
   static_assert(T >= 32, "tcgen05.ld/st run on whole warps");
@@ -181,14 +181,18 @@ struct TmShape {
   // (ONEBUF) 64 registers and ONE exchange buffer per CTA: four 256-thread
   // CTAs at 4096 (4 x 35 KB of shared memory, 4 x 128 TMEM columns), two
   // 512-thread CTAs at 8192 (2 x (70 + 32) KB: the buffer and the lane-pair
-  // pass's twiddle table; 2 x 256 TMEM columns).  The buffer's reuse by the
+  // pass's twiddle table; 2 x 256 TMEM columns), one 1024-thread CTA at
+  // 16384 (140 + 32 KB; all 512 columns) -- 32 warps per SM in each case.  The buffer's reuse by the
   // next transform waits on an mbarrier that every thread arrives on after
   // its last read (fft_cl_tmtw), so the wait falls a whole pass after the
   // arrivals.
   static constexpr bool ONEBUF = O && CL;
   static constexpr int MINB = O ? (ONEBUF ? 65536 / (64 * T) : T <= 256 ? 768 / T : 1) : X::MINB;
-  // lane-pair twiddles of N = 8192: float4 [4][T] (W^(b + 256 i), i < 8)
-  static constexpr size_t lp_bytes = ONEBUF && N == 8192 ? 4 * T * sizeof(float4) : 0;
+  // last-pass twiddles per thread: float4 [4][T] at 8192 (the lane-pair
+  // pass's W^(b + 256 i), i < 8), float4 [2][T] at 16384 (the radix-4 pass's
+  // W^m of its four butterflies)
+  static constexpr int lp_vec = ONEBUF ? (N == 8192 ? 4 : N == 16384 ? 2 : 0) : 0;
+  static constexpr size_t lp_bytes = (size_t)lp_vec * T * sizeof(float4);
   static constexpr size_t smem = ((X::DB || CL) && !ONEBUF ? 2 : 1) * X::buf_bytes + lp_bytes;
   template <int K>
   struct Cols {
@@ -418,6 +422,102 @@ __device__ __forceinline__ void fft_cl_tmtw(float2 (&v)[16], int t, float2* buf,
   }
 }
 
+// Barrier of the four warps 4 g .. 4 g + 3 (the two 16384-point classes 2 g,
+// 2 g + 1): named barrier 1 + g of 128 threads.
+__device__ __forceinline__ void class_pair_sync(int warp) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + (warp >> 2)) : "memory");
+}
+
+// The class-local 16384-point inverse transform (ClassLocal<16384>): the
+// radix-16 passes NS = 16 and 256 with their bases from TMEM columns ta ..
+// ta + 16, the radix-4 pass with W^m of its four butterflies from this
+// thread's column of the shared-memory table (W^2m, W^3m formed as in
+// TwBase<4>::init).  One CTA barrier, one barrier of the class's warps and two
+// __syncwarp per transform; the buffer's reuse waits on 'rel' as above.
+__device__ __forceinline__ void fft16384_cl_tmtw(float2 (&v)[16], int t, float2* buf, uint32_t ta_tw,
+                                                 BufRelease& rel, const float4* lp) {
+  constexpr int N = 16384, T = N / 16;
+  using CLq = ClassLocal<N>;
+  {
+    FftTw<N, 16, true, 1> none;  // pass 1 (NS = 1) takes no twiddles
+    pass_compute_tw<N, 16, 16, 1, true>(v, none);
+  }
+  buf_release_wait(rel);
+  {
+    float2* b = buf + pad_q(16 * t);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[u] = v[u];
+  }
+  float w[8];
+  tm_ld8(ta_tw, w);
+  __syncthreads();
+  const int jp = CLq::perm(t);
+  const float2* g = buf + pad_q(jp);  // element jp + T r sits at g[q_off(T r)]
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = g[q_off(T * r)];
+  {
+    tm_wait_ld8(w);
+    FftTw<N, 16, true, 16> tw;
+    tw.tw[0] = tw_unpack(w);
+    pass_compute_tw<N, 16, 16, 16, true>(v, tw);
+  }
+  tm_ld8(ta_tw + 8u, w);
+  const int warp = t >> 5;
+  class_pair_sync(warp);  // the class's warps have read every slot of the class
+  {
+    // butterfly jp of the NS = 16 pass writes y[(jp / 16) 256 + (jp mod 16) + 16 u]
+    float2* b = buf + pad_q((jp >> 4) * 256 + (jp & 15));
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[q_off(16 * u)] = v[u];
+  }
+  class_pair_sync(warp);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = g[q_off(T * r)];
+  {
+    tm_wait_ld8(w);
+    FftTw<N, 16, true, 256> tw;
+    tw.tw[0] = tw_unpack(w);
+    pass_compute_tw<N, 16, 16, 256, true>(v, tw);
+  }
+  const int h = jp >> 8, k = jp & 255;
+  __syncwarp();  // the four lanes of this k have read their slots
+  {
+    // butterfly jp of the NS = 256 pass writes y[4096 h + k + 256 u]
+    float2* b = buf + pad_q(4096 * h + k);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[q_off(256 * u)] = v[u];
+  }
+  __syncwarp();
+  {
+    // radix-4 butterfly i: m = k + 256 (h + 4 i), inputs x[m + 4096 s]
+    const float2* q = buf + pad_q(k + 256 * h);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) v[4 * i + s] = q[q_off(1024 * i + 4096 * s)];
+  }
+  buf_release_arrive(rel);  // the last read of the buffer in this transform
+  FftTw<N, 16, true, 4096> lt;
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    const float4 x = lp[T * hh + t];
+    lt.tw[2 * hh].a[0] = make_float2(x.x, x.y);
+    lt.tw[2 * hh + 1].a[0] = make_float2(x.z, x.w);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    lt.tw[i].a[1] = c_mul(lt.tw[i].a[0], lt.tw[i].a[0]);
+    lt.tw[i].a[2] = c_mul(lt.tw[i].a[1], lt.tw[i].a[0]);
+    float2 u[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) u[s] = v[4 * i + s];
+    TwApply<4, 1, false>::run(u, lt.tw[i]);
+    dft_r<4, true>(u);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) v[4 * i + s] = u[s];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // One CTA: PRNs p0 .. p0 + kk - 1 (kk <= K) of the tile rows u0 .. u0 + mm - 1
 // (mm <= M; a row is a Doppler bin, or the bin bin_order names).  Each bin
@@ -491,10 +591,10 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
   // and the lane-pair twiddles of N = 8192 into this thread's table column
   // (read back only by this thread)
   float4* lp = reinterpret_cast<float4*>(sm + X::buf_bytes / sizeof(float2));
-  if constexpr (Cl::tw_tmem && N == 8192) {
+  if constexpr (Cl::tw_tmem && Sh::lp_vec > 0) {
     const auto& lt = tw.next.next.next;
 #pragma unroll
-    for (int h = 0; h < 4; ++h)
+    for (int h = 0; h < Sh::lp_vec; ++h)
       lp[T * h + j] = make_float4(lt.tw[2 * h].a[0].x, lt.tw[2 * h].a[0].y, lt.tw[2 * h + 1].a[0].x,
                                   lt.tw[2 * h + 1].a[0].y);
   }
@@ -586,7 +686,8 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
             tm_product<E>(tq, v, v);
           }
           if constexpr (Cl::tw_tmem) {
-            fft_cl_tmtw<N, Sh::ONEBUF>(v, j, phase ? buf1 : buf0, ttw, rel, lp);
+            if constexpr (N == 16384) fft16384_cl_tmtw(v, j, buf0, ttw, rel, lp);
+            else fft_cl_tmtw<N, Sh::ONEBUF>(v, j, phase ? buf1 : buf0, ttw, rel, lp);
             phase ^= 1;
           } else if constexpr (CL) {
             fft_class_local<N, true>(v, j, phase ? buf1 : buf0, tw);
@@ -617,6 +718,7 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
           }
           continue;
         }
+        if constexpr (K > 1) {  // (one PRN per CTA always takes the block above)
 #pragma unroll 1
         for (int i = 0; i < kk; ++i) {
           if constexpr (X::TWC) tw.launder();
@@ -659,6 +761,7 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
           } else {
             tm_accumulate32(tsum + (uint32_t)(E * i), v, t == 0);
           }
+        }
         }
       }
       // R = IFFT / N, so |R|^2 = |.|^2 / N^2 (an exact power of two)
@@ -828,7 +931,7 @@ static cudaError_t tm_launch_batch(const BatchGroup& g, cudaStream_t stream) {
   CALL(4096, 16, 2, 2, false) CALL(4096, 16, 1, 1, true)                                                   \
   CALL(8192, 16, 1, 1, false) CALL(8192, 16, 2, 1, false) CALL(8192, 16, 1, 2, false)                      \
   CALL(8192, 16, 2, 2, false) CALL(8192, 16, 1, 1, true)                                                  \
-  CALL(16384, 32, 1, 1, false) CALL(16384, 32, 1, 2, false)
+  CALL(16384, 32, 1, 1, false) CALL(16384, 32, 1, 2, false) CALL(16384, 16, 1, 1, true)
 
 static bool tm_shape(int N, int code, int* E, int* K, int* M, bool* O) {
   if (!(code & (int)GNSS_TUNE_TMEM)) return false;
