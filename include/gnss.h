@@ -577,8 +577,19 @@ GNSS_API gnss_status gnss_server_get_stats(gnss_server* srv, gnss_server_stats* 
  * load feeds k products and transforms; 1 at 16384) and GNSS_TUNE_BINS(m)
  * Doppler bins per CTA (m = 1 or 2, run one after another with the code
  * spectra kept).  It gives the register form's surfaces and records bit for
- * bit.  A shape is valid only where the CTA's tensor-memory columns fit its
- * share of the register file (so co-resident CTAs never wait for columns).
+ * bit.  GNSS_TUNE_OCC (one PRN and bin per CTA; N = 2048, 4096, 8192, 16384
+ * with 16 per thread) is its occupancy form: the sums read from tensor memory
+ * only after each transform and no prefetch, so more CTAs fit an SM -- six
+ * of 128 threads at 2048; at 4096, 8192 and 16384 the class-local schedule
+ * at 64 registers with one shared-memory exchange buffer per CTA (four CTAs
+ * of 256, two of 512, one of 1024 threads: 32 warps per SM), the twiddle
+ * bases in tensor memory too, the default at those sizes.  Bit-identical to
+ * the register form at 2048-8192; at 16384 it factors the transform as
+ * radix 16-16-16-4 (the register forms there use 32 per thread), so its
+ * surfaces agree with the others to rounding.  A shape is valid only where
+ * the tensor-memory columns of the CTAs that fit one SM together (registers,
+ * shared memory, threads) total at most 512, so co-resident CTAs never wait
+ * for columns.
  *
  * With force_elems = 0 every valid variant is timed on a probe shaped like
  * the plan (its Doppler bins up to 32, its sets, 8 blocks) and the fastest
@@ -589,7 +600,7 @@ GNSS_API gnss_status gnss_server_get_stats(gnss_server* srv, gnss_server_stats* 
 #define GNSS_TUNE_STAGED 0x100u
 #define GNSS_TUNE_CLASS_LOCAL 0x200u
 #define GNSS_TUNE_TMEM 0x400u
-#define GNSS_TUNE_OCC 0x800u /* TMEM variant, one PRN and bin: one more CTA per SM */
+#define GNSS_TUNE_OCC 0x800u /* TMEM variant, one PRN and bin: the occupancy form (more CTAs per SM) */
 #define GNSS_TUNE_PRNS(k) ((((uint32_t)(k)) - 1u) << 12) /* PRNs per CTA (TMEM variant) */
 #define GNSS_TUNE_BINS(m) ((((uint32_t)(m)) - 1u) << 14) /* Doppler bins per CTA (TMEM variant) */
 typedef struct {

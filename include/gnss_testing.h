@@ -34,9 +34,9 @@ GNSS_API gnss_status gnss_probe_ffma(int iters, double* tflops, double* ms, void
  * Errors: GNSS_ECUDA. */
 GNSS_API gnss_status gnss_testing_set_stage_wait_limit(uint32_t iters, void* stream);
 
-/* Testing hook: every wait of the correlate's occupancy form at N = 4096
- * (variant code 16 | GNSS_TUNE_TMEM | GNSS_TUNE_OCC, one shared-memory
- * exchange buffer per CTA) for the release of that buffer by the CTA's other
+/* Testing hook: every wait of the correlate's occupancy form at N = 4096,
+ * 8192 and 16384 (variant code 16 | GNSS_TUNE_TMEM | GNSS_TUNE_OCC, one
+ * shared-memory exchange buffer per CTA) for the release of that buffer by the CTA's other
  * warps polls at most 'iters' times before it gives up (default 4194304; 0
  * makes every wait give up at once).  A wait that gave up flags its call's
  * records with GNSS_DET_WAIT_TIMEOUT and the CTA goes on: its warps may then

@@ -498,9 +498,9 @@ def set_stage_wait_limit(iters: int, stream=None) -> None:
 
 def set_buf_wait_limit(iters: int, stream=None) -> None:
     """gnss_testing_set_buf_wait_limit (a testing hook): polls of each wait of
-    the 4096-point occupancy form for its exchange buffer's release (0: every
-    wait gives up at once and the call's records are flagged WAIT_TIMEOUT;
-    the default is 4194304)."""
+    the class-local occupancy forms (4096, 8192, 16384) for their exchange
+    buffer's release (0: every wait gives up at once and the call's records
+    are flagged WAIT_TIMEOUT; the default is 4194304)."""
     check(load().gnss_testing_set_buf_wait_limit(iters, _stream_ptr(stream)), "gnss_testing_set_buf_wait_limit")
 
 

@@ -602,12 +602,13 @@ struct ClassLocal {
 //
 // Thread position p within the class runs butterfly J = c + 16 i', where i'
 // takes p's bits in the order (0, 5, 1, 2, 4, 3); slot of element i:
-// i + i/16 + i/256 + i/4096.  A CPU check of every access of the schedule
-// (first-pass stores at 16 t + u, class gathers at J + 1024 r, class stores
-// at 256 (J / 16) + J mod 16 + 16 u, quad stores at 4096 h + k + 256 u, quad
-// gathers at k + 256 (h + 4 i) + 4096 s) found each half-warp on 16
-// distinct 8-byte bank pairs, and every offset from a thread's base is a
-// compile-time constant (no carries).
+// i + i/16 + i/256 + i/4096.  Every access of the schedule (first-pass
+// stores at 16 t + u, class gathers at J + 1024 r, class stores at
+// 256 (J / 16) + J mod 16 + 16 u, quad stores at 4096 h + k + 256 u, quad
+// gathers at k + 256 (h + 4 i) + 4096 s) puts each half-warp on 16 distinct
+// 8-byte bank pairs, and every offset from a thread's base is a compile-time
+// constant (no carries); tests/test_schedule_16384.py models the schedule on
+// the host and checks both, the exchange groups and the output order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int pad_q(int i) { return i + (i >> 4) + (i >> 8) + (i >> 12); }
 // pad_q(x + d) - pad_q(x) for the strides d of the 16384 schedule (no carries)
