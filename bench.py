@@ -612,6 +612,18 @@ def run_variants(g, torch, rec, stream, flush, steps=20):
     return out
 
 
+def _serve_points(spec, seconds):
+    """'rate[:seconds],...' -> [(rate, seconds)]; a point without its own
+    duration runs for 'seconds'."""
+    out = []
+    for item in spec.split(","):
+        item = item.strip()
+        if item:
+            r, _, sec = item.partition(":")
+            out.append((float(r), float(sec) if sec else float(seconds)))
+    return out
+
+
 def run_serving_curve(g, serve, rates, seconds, bound_ms, seed=1309005205):
     """Latency against offered load through gnss_submit / gnss_poll: one
     server (plans and code spectra made resident once, before timing) takes
@@ -627,7 +639,7 @@ def run_serving_curve(g, serve, rates, seconds, bound_ms, seed=1309005205):
     req_cells = [_cells(32, r.n_dopp, r.N, r.n_blocks, r.coh_ms) for r in serve]
     rng = np.random.default_rng(seed)
     points = []
-    for rate in rates:
+    for rate, seconds in rates:
         pending, done, done_cells, queued = {}, [], [0], []
         refused = 0
         lock = threading.Lock()
@@ -896,7 +908,7 @@ def run_ours(args):
     if batch:
         line["batch"] = run_batch(g, torch, batch, stream, flush, steps=3, peak_tflops=peak_tflops)
     if serve:
-        line["serving"] = run_serving_curve(g, serve, [float(r) for r in args.serve_rates.split(",") if r.strip()],
+        line["serving"] = run_serving_curve(g, serve, _serve_points(args.serve_rates, args.serve_seconds),
                                             args.serve_seconds, args.serve_bound_ms)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(rec, args)
@@ -1077,8 +1089,9 @@ def main():
     ap.add_argument("--variants", action="store_true",
                     help="also time every correlate variant the GPU accepts (100 ms request, N = 2048 ... 16384)")
     ap.add_argument("--batch-requests", type=int, default=256)
-    ap.add_argument("--serve-rates", default="50,100,150,175,200,250",
-                    help="offered request rates of the serving curve (requests/s)")
+    ap.add_argument("--serve-rates", default="50,100,150,175,200,250,500:5,1000:5,2000:5",
+                    help="offered request rates of the serving curve (requests/s), each 'rate' or "
+                         "'rate:seconds' (overload points run shorter)")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="seconds of Poisson arrivals per rate")
     ap.add_argument("--serve-pool", type=int, default=64, help="distinct recordings in the serving pool")
     ap.add_argument("--serve-bound-ms", type=int, default=250,

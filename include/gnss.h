@@ -579,12 +579,12 @@ GNSS_API gnss_status gnss_server_get_stats(gnss_server* srv, gnss_server_stats* 
  * spectra kept).  It gives the register form's surfaces and records bit for
  * bit.  GNSS_TUNE_OCC (one PRN and bin per CTA; N = 2048, 4096, 8192, 16384
  * with 16 per thread) is its occupancy form: the sums read from tensor memory
- * only after each transform and no prefetch, so more CTAs fit an SM -- six
- * of 128 threads at 2048; at 4096, 8192 and 16384 the class-local schedule
- * at 64 registers with one shared-memory exchange buffer per CTA (four CTAs
- * of 256, two of 512, one of 1024 threads: 32 warps per SM), the twiddle
- * bases in tensor memory too, the default at those sizes.  Bit-identical to
- * the register form at 2048-8192; at 16384 it factors the transform as
+ * only after each transform and no prefetch, so more CTAs fit an SM: the
+ * class-local schedule at 64 registers with one shared-memory exchange
+ * buffer per CTA (eight CTAs of 128 threads at 2048, four of 256, two of
+ * 512, one of 1024: 32 warps per SM), the twiddle bases in tensor memory
+ * too; the default at 4096, 8192 and 16384.  Bit-identical to the register
+ * form at 2048-8192; at 16384 it factors the transform as
  * radix 16-16-16-4 (the register forms there use 32 per thread), so its
  * surfaces agree with the others to rounding.  A shape is valid only where
  * the tensor-memory columns of the CTAs that fit one SM together (registers,

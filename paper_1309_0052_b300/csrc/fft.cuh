@@ -607,7 +607,7 @@ struct ClassLocal {
 // 256 (J / 16) + J mod 16 + 16 u, quad stores at 4096 h + k + 256 u, quad
 // gathers at k + 256 (h + 4 i) + 4096 s) puts each half-warp on 16 distinct
 // 8-byte bank pairs, and every offset from a thread's base is a compile-time
-// constant (no carries); tests/test_schedule_16384.py models the schedule on
+// constant (no carries); tests/test_class_local_schedules.py models the schedule on
 // the host and checks both, the exchange groups and the output order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int pad_q(int i) { return i + (i >> 4) + (i >> 8) + (i >> 12); }
@@ -634,6 +634,41 @@ struct ClassLocal<16384> {
     constexpr float scale = (INV ? 2.f : -2.f) / float(N);
 #pragma unroll
     for (int i = 0; i < 4; ++i) last.tw[i].init(scale * float(quad_m(jp, i)));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Class-local schedule at N = 2048 (16 per thread, T = 128): radix 16, 16,
+// then 8.  After the CTA-wide exchange class c = J mod 16 (128 elements)
+// lives on 8 lanes of one warp, which run the NS = 16 pass and exchange in
+// place under __syncwarp; the gather after it gives thread jp the inputs of
+// its two radix-8 butterflies jp and jp + 128 of the last pass (x[jp + 128 r]),
+// so that pass needs no exchange and ends with X[jp + 128 r] in v[r].
+//
+// Thread t's class index jp = c + 16 i takes c from t's bits (0, 1, 5, 6) and
+// i from its bits (4, 2, 3); slot of element e: e + e/8 + e/128.  With these
+// every access (first-pass stores at 16 t + u, class gathers at jp + 128 r,
+// class stores at 256 (jp / 16) + jp mod 16 + 16 u) puts each half-warp on 16
+// distinct 8-byte bank pairs and every offset from a thread's base is a
+// compile-time constant (tests/test_class_local_schedules.py models it too).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pad_2k(int e) { return e + (e >> 3) + (e >> 7); }
+// pad_2k(x + d) - pad_2k(x) for the strides d of the 2048 schedule (no carries)
+__host__ __device__ constexpr int off_2k(int d) { return d + d / 8 + d / 128; }
+
+template <>
+struct ClassLocal<2048> {
+  static constexpr int N = 2048, E = 16, T = N / E, G = 8;
+  static constexpr int smem_elems = N + N / 8 + N / 128;  // > pad_2k(N - 1)
+  __device__ __forceinline__ static int perm(int t) {
+    const int c = (t & 3) | (((t >> 5) & 3) << 2);
+    const int i = ((t >> 4) & 1) | (((t >> 2) & 3) << 1);
+    return c + 16 * i;
+  }
+  __device__ __forceinline__ static int out_index(int jp, int r) { return jp + T * r; }
+  template <bool INV>
+  __device__ __forceinline__ static void init_twiddles(FftTw<N, 16, INV>& tw, int jp) {
+    tw.init(jp);  // NS = 16: k = jp mod 16; NS = 256 (radix 8): butterflies jp + 128 q
   }
 };
 

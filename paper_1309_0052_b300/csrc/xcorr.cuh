@@ -47,8 +47,8 @@ struct Cfg {
 // E = 16: one CTA barrier per block; fft_class_local).
 template <int N, int E, bool ST = false, bool CL = false>
 struct XCfg {
-  static_assert(!CL || ((N == 4096 || N == 8192 || N == 16384) && E == 16 && !ST),
-                "class-local schedule: N = 4096, 8192 or 16384");
+  static_assert(!CL || ((N == 2048 || N == 4096 || N == 8192 || N == 16384) && E == 16 && !ST),
+                "class-local schedule: N = 2048 ... 16384");
   static constexpr int T = N / E;
   static constexpr bool TWC = (E <= 16);                        // twiddle bases cached in registers
   static constexpr size_t buf_bytes =

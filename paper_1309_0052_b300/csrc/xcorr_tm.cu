@@ -169,7 +169,7 @@ __host__ __device__ constexpr int tm_pow2_cols(int c) { return c <= 32 ? 32 : 2 
 
 template <int N, int E, bool O = false>
 struct TmShape {
-  static constexpr bool CL = (N == 4096 || N == 8192 || (N == 16384 && O)) && E == 16;
+  static constexpr bool CL = (N == 4096 || N == 8192 || ((N == 2048 || N == 16384) && O)) && E == 16;
   using X = XCfg<N, E, false, CL>;
   static constexpr int T = N / E;
   static_assert(T >= 32, "tcgen05.ld/st run on whole warps");
@@ -182,7 +182,8 @@ struct TmShape {
   // CTAs at 4096 (4 x 35 KB of shared memory, 4 x 128 TMEM columns), two
   // 512-thread CTAs at 8192 (2 x (70 + 32) KB: the buffer and the lane-pair
   // pass's twiddle table; 2 x 256 TMEM columns), one 1024-thread CTA at
-  // 16384 (140 + 32 KB; all 512 columns) -- 32 warps per SM in each case.  The buffer's reuse by the
+  // 16384 (140 + 32 KB; all 512 columns), eight 128-thread CTAs at 2048
+  // (8 x (18 + 8) KB, 8 x 64 columns) -- 32 warps per SM in each case.  The buffer's reuse by the
   // next transform waits on an mbarrier that every thread arrives on after
   // its last read (fft_cl_tmtw), so the wait falls a whole pass after the
   // arrivals.
@@ -190,8 +191,9 @@ struct TmShape {
   static constexpr int MINB = O ? (ONEBUF ? 65536 / (64 * T) : T <= 256 ? 768 / T : 1) : X::MINB;
   // last-pass twiddles per thread: float4 [4][T] at 8192 (the lane-pair
   // pass's W^(b + 256 i), i < 8), float4 [2][T] at 16384 (the radix-4 pass's
-  // W^m of its four butterflies)
-  static constexpr int lp_vec = ONEBUF ? (N == 8192 ? 4 : N == 16384 ? 2 : 0) : 0;
+  // W^m of its four butterflies), float4 [4][T] at 2048 (the radix-8 pass's
+  // bases w, w^2, w^3, w^4 of its two butterflies)
+  static constexpr int lp_vec = ONEBUF ? (N == 8192 || N == 2048 ? 4 : N == 16384 ? 2 : 0) : 0;
   static constexpr size_t lp_bytes = (size_t)lp_vec * T * sizeof(float4);
   static constexpr size_t smem = ((X::DB || CL) && !ONEBUF ? 2 : 1) * X::buf_bytes + lp_bytes;
   template <int K>
@@ -518,6 +520,60 @@ __device__ __forceinline__ void fft16384_cl_tmtw(float2 (&v)[16], int t, float2*
   }
 }
 
+// The class-local 2048-point inverse transform (ClassLocal<2048>): the
+// NS = 16 pass's bases from TMEM columns ta .. ta + 8, the radix-8 NS = 256
+// pass's bases (w, w^2, w^3 and w^4 of butterflies jp and jp + 128) from this
+// thread's column of the shared-memory table.  One CTA barrier and two
+// __syncwarp per transform; the buffer's reuse waits on 'rel'.
+__device__ __forceinline__ void fft2048_cl_tmtw(float2 (&v)[16], int t, float2* buf, uint32_t ta_tw,
+                                                BufRelease& rel, const float4* lp) {
+  constexpr int N = 2048, T = N / 16;
+  {
+    FftTw<N, 16, true, 1> none;  // pass 1 (NS = 1) takes no twiddles
+    pass_compute_tw<N, 16, 16, 1, true>(v, none);
+  }
+  buf_release_wait(rel);
+  {
+    float2* b = buf + pad_2k(16 * t);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[off_2k(u)] = v[u];
+  }
+  float w[8];
+  tm_ld8(ta_tw, w);
+  __syncthreads();
+  const int jp = ClassLocal<N>::perm(t);
+  const float2* g = buf + pad_2k(jp);  // element jp + T r sits at g[off_2k(T r)]
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = g[off_2k(T * r)];
+  {
+    tm_wait_ld8(w);
+    FftTw<N, 16, true, 16> tw;
+    tw.tw[0] = tw_unpack(w);
+    pass_compute_tw<N, 16, 16, 16, true>(v, tw);
+  }
+  __syncwarp();  // the class's eight lanes have read every slot of the class
+  {
+    // butterfly jp of the NS = 16 pass writes y[(jp / 16) 256 + (jp mod 16) + 16 u]
+    float2* b = buf + pad_2k((jp >> 4) * 256 + (jp & 15));
+#pragma unroll
+    for (int u = 0; u < 16; ++u) b[off_2k(16 * u)] = v[u];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = g[off_2k(T * r)];
+  buf_release_arrive(rel);  // the last read of the buffer in this transform
+  FftTw<N, 16, true, 256> lt;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float4 x0 = lp[T * (2 * q) + t], x1 = lp[T * (2 * q + 1) + t];
+    lt.tw[q].a[0] = make_float2(x0.x, x0.y);
+    lt.tw[q].a[1] = make_float2(x0.z, x0.w);
+    lt.tw[q].a[2] = make_float2(x1.x, x1.y);
+    lt.tw[q].b[0] = make_float2(x1.z, x1.w);
+  }
+  pass_compute_tw<N, 16, 8, 256, true>(v, lt);
+}
+
 // ---------------------------------------------------------------------------
 // One CTA: PRNs p0 .. p0 + kk - 1 (kk <= K) of the tile rows u0 .. u0 + mm - 1
 // (mm <= M; a row is a Doppler bin, or the bin bin_order names).  Each bin
@@ -587,11 +643,21 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
   }
   // with the twiddle bases in TMEM: the two twiddled passes' bases, after the PRNs' columns
   const uint32_t ttw = tq + (uint32_t)(K * Cl::per_prn);
-  if constexpr (Cl::tw_tmem) tw_to_tmem(tw.next.tw[0], tw.next.next.tw[0], ttw);
+  if constexpr (Cl::tw_tmem) {
+    if constexpr (N == 2048) tw_to_tmem(tw.next.tw[0], tw.next.tw[0], ttw);  // (the NS = 16 bases only)
+    else tw_to_tmem(tw.next.tw[0], tw.next.next.tw[0], ttw);
+  }
   // and the lane-pair twiddles of N = 8192 into this thread's table column
   // (read back only by this thread)
   float4* lp = reinterpret_cast<float4*>(sm + X::buf_bytes / sizeof(float2));
-  if constexpr (Cl::tw_tmem && Sh::lp_vec > 0) {
+  if constexpr (Cl::tw_tmem && N == 2048) {
+    const auto& lt = tw.next.next;  // NS = 256, radix 8: w, w^2, w^3 and w^4 of two butterflies
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      lp[T * (2 * q) + j] = make_float4(lt.tw[q].a[0].x, lt.tw[q].a[0].y, lt.tw[q].a[1].x, lt.tw[q].a[1].y);
+      lp[T * (2 * q + 1) + j] = make_float4(lt.tw[q].a[2].x, lt.tw[q].a[2].y, lt.tw[q].b[0].x, lt.tw[q].b[0].y);
+    }
+  } else if constexpr (Cl::tw_tmem && Sh::lp_vec > 0) {
     const auto& lt = tw.next.next.next;
 #pragma unroll
     for (int h = 0; h < Sh::lp_vec; ++h)
@@ -687,6 +753,7 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
           }
           if constexpr (Cl::tw_tmem) {
             if constexpr (N == 16384) fft16384_cl_tmtw(v, j, buf0, ttw, rel, lp);
+            else if constexpr (N == 2048) fft2048_cl_tmtw(v, j, buf0, ttw, rel, lp);
             else fft_cl_tmtw<N, Sh::ONEBUF>(v, j, phase ? buf1 : buf0, ttw, rel, lp);
             phase ^= 1;
           } else if constexpr (CL) {

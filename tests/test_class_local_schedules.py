@@ -1,11 +1,11 @@
-"""Host-side model of the 16384-point class-local schedule of the correlate's
-occupancy form (the shared-memory slots, thread -> butterfly map, exchange
-groups and output order written in csrc/fft.cuh and csrc/xcorr_tm.cu),
-checked without a GPU:
+"""Host-side models of the 16384- and 2048-point class-local schedules of the
+correlate's occupancy form (the shared-memory slots, thread -> butterfly map,
+exchange groups and output order written in csrc/fft.cuh and
+csrc/xcorr_tm.cu), checked without a GPU:
 
 * the model's transform, pass by pass through the padded slots, equals the
   inverse DFT (numpy) -- so the addresses, twiddle exponents and output order
-  are those of a Stockham radix 16-16-16-4 inverse transform;
+  are those of a Stockham radix 16-16-16-4 (16-16-8) inverse transform;
 * each in-place exchange writes exactly the slots its synchronising group
   read (the class pair's four warps; the four lanes of one residue, which
   share a warp), so the named barrier and __syncwarp guard every reuse;
@@ -155,3 +155,86 @@ def test_every_warp_access_is_free_of_bank_conflicts():
         for ws in warps:
             for a in range(16):
                 assert _wavefronts([pad_q(f(t, a)) for t in ws]) == 2, (name, ws[0], a)
+
+
+# --- N = 2048: radix 16-16-8, T = 128, classes on 8 lanes of one warp --------
+N2, T2 = 2048, 128
+SMEM2 = N2 + N2 // 8 + N2 // 128
+
+
+def pad_2k(e):
+    return e + (e >> 3) + (e >> 7)
+
+
+def off_2k(d):
+    return d + d // 8 + d // 128
+
+
+def perm_2k(t):
+    c = (t & 3) | (((t >> 5) & 3) << 2)
+    i = ((t >> 4) & 1) | (((t >> 2) & 3) << 1)
+    return c + 16 * i
+
+
+JP2 = [perm_2k(t) for t in range(T2)]
+
+
+def test_2048_map_is_a_bijection_with_each_class_in_one_warp():
+    assert sorted(JP2) == list(range(T2))
+    warps = {}
+    for t in range(T2):
+        warps.setdefault(JP2[t] % 16, set()).add(t >> 5)
+    assert all(len(w) == 1 for w in warps.values()) and len(warps) == 16
+
+
+def test_2048_model_equals_inverse_dft_and_classes_stay_in_their_warp():
+    rng = np.random.default_rng(2048)
+    x = rng.standard_normal(N2) + 1j * rng.standard_normal(N2)
+    buf = np.full(SMEM2, np.nan, complex)
+    t_all = np.arange(T2)
+    v = _dft(x[t_all[:, None] + T2 * np.arange(16)[None, :]])  # pass 1, NS = 1
+    for t in range(T2):
+        s = [pad_2k(16 * t) + off_2k(u) for u in range(16)]
+        assert s == [pad_2k(16 * t + u) for u in range(16)]
+        buf[s] = v[t]
+    read = {}
+    for t in range(T2):
+        g = [pad_2k(JP2[t]) + off_2k(T2 * r) for r in range(16)]
+        assert g == [pad_2k(JP2[t] + T2 * r) for r in range(16)] and max(g) < SMEM2
+        v[t] = buf[g]
+        read.setdefault((t >> 5, JP2[t] % 16), set()).update(g)
+    v = _dft(v * _w(256, np.outer(np.array(JP2) % 16, np.arange(16))))  # NS = 16
+    wrote = {}
+    for t in range(T2):
+        jp = JP2[t]
+        base = pad_2k((jp >> 4) * 256 + (jp & 15))
+        s = [base + off_2k(16 * u) for u in range(16)]
+        assert s == [pad_2k((jp >> 4) * 256 + (jp & 15) + 16 * u) for u in range(16)]
+        buf[s] = v[t]
+        wrote.setdefault((t >> 5, jp % 16), set()).update(s)
+    assert read == wrote  # the class's lanes (one warp) overwrite only what they read
+    for t in range(T2):
+        v[t] = buf[[pad_2k(JP2[t]) + off_2k(T2 * r) for r in range(16)]]
+    out = np.full(N2, np.nan, complex)
+    for t in range(T2):
+        jp = JP2[t]
+        for q in range(2):  # radix-8 butterflies J = jp + 128 q (NS = 256): inputs v[q + 2 s]
+            J = jp + 128 * q
+            u = _dft(v[t][q::2] * _w(2048, J * np.arange(8)))
+            for k in range(8):
+                out[J + 256 * k] = u[k]  # = X[jp + 128 (q + 2 k)]
+    ref = np.fft.ifft(x) * N2
+    assert not np.isnan(out).any()
+    assert np.abs(out - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_2048_every_warp_access_is_free_of_bank_conflicts():
+    pats = {
+        "first-pass stores": lambda t, a: 16 * t + a,
+        "class gathers": lambda t, a: JP2[t] + T2 * a,
+        "class stores": lambda t, a: 256 * (JP2[t] >> 4) + (JP2[t] & 15) + 16 * a,
+    }
+    for name, f in pats.items():
+        for w in range(T2 // 32):
+            for a in range(16):
+                assert _wavefronts([pad_2k(f(t, a)) for t in range(w * 32, w * 32 + 32)]) == 2, (name, w, a)

@@ -439,7 +439,7 @@ def test_staged_wait_gives_up_safely(g):
         plan.autotune(_default(4096))
 
 
-@pytest.mark.parametrize("N", [4096, 8192, 16384])
+@pytest.mark.parametrize("N", [2048, 4096, 8192, 16384])
 def test_buffer_release_wait_gives_up_safely(g, N):
     """The class-local occupancy forms keep one exchange buffer per CTA; the
     next transform's stores wait (bounded) for every warp's release of it.
