@@ -176,17 +176,18 @@ struct TmShape {
   static constexpr int WARPS = T / 32;
   static constexpr int SLOTS = WARPS >= 4 ? WARPS / 4 : 1;  // warps sharing a lane quarter
   // The occupancy form (O): more CTAs per SM, so more warps hide latency --
-  // the sums in TMEM, no register prefetch, and registers capped at 80 for
-  // three 256-thread CTAs (six of 128).  With the class-local schedule
-  // (ONEBUF) 64 registers and ONE exchange buffer per CTA: four 256-thread
-  // CTAs at 4096 (4 x 35 KB of shared memory, 4 x 128 TMEM columns), two
-  // 512-thread CTAs at 8192 (2 x (70 + 32) KB: the buffer and the lane-pair
-  // pass's twiddle table; 2 x 256 TMEM columns), one 1024-thread CTA at
-  // 16384 (140 + 32 KB; all 512 columns), eight 128-thread CTAs at 2048
-  // (8 x (18 + 8) KB, 8 x 64 columns) -- 32 warps per SM in each case.  The buffer's reuse by the
-  // next transform waits on an mbarrier that every thread arrives on after
-  // its last read (fft_cl_tmtw), so the wait falls a whole pass after the
-  // arrivals.
+  // the sums in TMEM and no register prefetch.  Every size it is built for
+  // runs the class-local schedule (ONEBUF) at 64 registers with ONE exchange
+  // buffer per CTA (without it the form would cap registers at 80 for three
+  // 256-thread CTAs): eight 128-thread CTAs at 2048 (8 x (18 + 8) KB of
+  // shared memory: the buffer and the radix-8 pass's bases; 8 x 64 TMEM
+  // columns), four 256-thread CTAs at 4096 (4 x 35 KB, 4 x 128 columns), two
+  // 512-thread CTAs at 8192 (2 x (70 + 32) KB with the lane-pair pass's
+  // twiddle table; 2 x 256 columns), one 1024-thread CTA at 16384 (140 + 32
+  // KB; all 512 columns) -- 32 warps per SM in each case.  The buffer's reuse
+  // by the next transform waits on an mbarrier that every thread arrives on
+  // after its last read (fft_cl_tmtw), so the wait falls a whole pass after
+  // the arrivals.
   static constexpr bool ONEBUF = O && CL;
   static constexpr int MINB = O ? (ONEBUF ? 65536 / (64 * T) : T <= 256 ? 768 / T : 1) : X::MINB;
   // last-pass twiddles per thread: float4 [4][T] at 8192 (the lane-pair
@@ -768,7 +769,7 @@ __device__ __forceinline__ void xcorr_tile_tm(const XcorrArgs& a, int cta, float
             add_power<E>(racc, v);
           } else if constexpr (E == 16) {
             // the sums are fetched only now: 16 registers fewer live through
-            // the transform (the occupancy form runs at 64 or 80 registers)
+            // the transform (the occupancy form runs at 64 registers)
             float s16[16];
             if (t > 0) {
               tm_wait_st();
